@@ -1,0 +1,173 @@
+/*
+ * mrcm.h -- C ABI of a GB300 (sm_103a) implementation of the Multiscale Robin
+ * Coupled Method with Oversampling and Smoothing (MRCM-OS, arXiv 2404.13811)
+ * for single-phase Darcy flow  u = -K grad p,  div u = f  (Sec. 2, Eqs. (1a)-(1d)).
+ *
+ * Call order (enforced; an out-of-order call returns MRCM_ERR_STATE):
+ *   mrcm_create / mrcm_create_batch
+ *   mrcm_build_basis       Algorithm 1, Steps 1-4 (and 6 when alpha_smooth != alpha_basis)
+ *   mrcm_solve_interface   Algorithm 1, Step 5
+ *   mrcm_smooth            Algorithm 1, Step 7 (any number of calls; additive in n_steps)
+ *   mrcm_fluxes            read the current solution (any time after mrcm_solve_interface)
+ *   mrcm_destroy
+ *
+ * Conventions
+ *   Cells are addressed x fastest: cell (ix, iy, iz) has flat index
+ *   ix + n[0] * (iy + n[1] * iz).  Arrays of cell data are dense in that order.
+ *   Sides are numbered x-, x+, y-, y+, z-, z+ (side id = 2 * axis + s).
+ *   Velocities are returned per cell and per side as the OUTWARD normal
+ *   velocity of that cell (array [ncells][2 * dim]); across the subdomain
+ *   skeleton they come from each cell's own subdomain and are double-valued,
+ *   as in the method (Sec. 2.1).
+ *   Every call runs asynchronously on the CUDA stream given at creation,
+ *   except where a call states that it synchronises.
+ *   Handles are not thread safe.  No exception or abort crosses this ABI:
+ *   every entry point returns 0 (MRCM_OK) or a negative MRCM_ERR_* code and
+ *   mrcm_last_error() describes the last failure.
+ *   Device memory for factors, bases, interface system and state is owned by
+ *   the handle (allocated in mrcm_create*, freed in mrcm_destroy).  Inputs are
+ *   copied at creation; output buffers belong to the caller.
+ */
+#ifndef MRCM_H
+#define MRCM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRCM_OK 0
+#define MRCM_ERR_BAD_INPUT (-1)      /* invalid sizes, K <= 0 or not finite, partition mismatch */
+#define MRCM_ERR_STATE (-2)          /* call out of order */
+#define MRCM_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define MRCM_ERR_NOT_SPD (-4)        /* non-positive pivot in a local factorisation */
+#define MRCM_ERR_NO_CONVERGENCE (-5) /* iterative refinement did not reach ir_tol in max_ir steps */
+#define MRCM_ERR_SINGULAR (-6)       /* zero pivot in the interface factorisation */
+#define MRCM_ERR_UNSUPPORTED (-7)    /* a size or option this build does not handle */
+#define MRCM_ERR_NOMEM (-8)          /* device allocation failed */
+
+#define MRCM_NEUMANN 0   /* u.n = value on the side (Eq. (1d)) */
+#define MRCM_DIRICHLET 1 /* p = value on the side (Eq. (1c)) */
+
+#define MRCM_P0 0 /* piecewise-constant interface spaces per coarse edge/face (Sec. 2.1) */
+#define MRCM_P1 1 /* piecewise-linear: {1, t} on edges (2D), {1, s, t} on faces (3D) */
+
+#define MRCM_FP64 0  /* local factorisations and solves in FP64 */
+#define MRCM_MIXED 1 /* FP32 local factor/solves + FP64 residuals (iterative refinement) */
+
+/* Cartesian grid: cells per axis and cell size per axis (dim = 2 or 3). */
+typedef struct {
+    int dim;
+    int n[3];
+    double h[3];
+} mrcm_grid;
+
+/* Boundary data per side (x-, x+, y-, y+, z-, z+): kind MRCM_NEUMANN with the
+ * outward normal velocity z, or MRCM_DIRICHLET with the pressure g; constant
+ * per side (Eqs. (1c)-(1d)). */
+typedef struct {
+    int kind[6];
+    double value[6];
+} mrcm_bc;
+
+/* Non-overlapping partition into blocks of sub[a] cells (must divide n[a]);
+ * each block Omega_i is oversampled by `overlap` cells per side, clipped at
+ * the domain boundary (hat-Omega_i, Sec. 2.1).  Smoothing requires
+ * 0 < 2 * overlap < sub[a]. */
+typedef struct {
+    int sub[3];
+    int overlap;
+} mrcm_partition;
+
+/* Method parameters.
+ *   space        MRCM_P0 / MRCM_P1: the polynomial space used for the Robin
+ *                data lambda^k on d hat-Omega_i and for M_H = V_H (Prop. 1
+ *                needs the same number of functions per edge in all three).
+ *   alpha_basis  Robin parameter for the basis and particular problems:
+ *                beta = alpha H / K_H, K_H the harmonic mean of the two
+ *                cells at the face, H the subdomain width normal to the face
+ *                (Sec. 2.1, after Eq. (genRobin)).
+ *   alpha_smooth the same for the smoothing solves (Sec. 3 uses 1).
+ *   precision    MRCM_FP64 or MRCM_MIXED.
+ *   ir_tol       relative residual (inf-norm) at which refinement stops
+ *                (mixed local solves and the interface solve).
+ *   max_ir       maximum refinement steps. */
+typedef struct {
+    int space;
+    double alpha_basis;
+    double alpha_smooth;
+    int precision;
+    double ir_tol;
+    int max_ir;
+} mrcm_params;
+
+typedef struct mrcm_handle mrcm_handle;
+
+/* Creates a handle for one problem.
+ *   K, f         cell permeability (> 0, finite) and source density f of
+ *                Eq. (1b) (the cell equation uses f * cell volume), [ncells].
+ *   device_ptrs  0: K and f are host pointers; 1: device pointers.
+ *   cuda_stream  cudaStream_t on which all work of this handle runs (0 = legacy default).
+ * Copies K and f, plans the decomposition, colours and interface ordering,
+ * and allocates all device memory of the handle.  Synchronises the stream. */
+int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
+                const mrcm_partition* part, const mrcm_params* params, int device_ptrs,
+                void* cuda_stream, mrcm_handle** out);
+
+/* Creates one handle for `count` independent problems (an ensemble).  Arrays
+ * grids, bcs, parts have `count` entries; K[m], f[m] point at member m's
+ * cells.  All members share `params`.  Every later call processes all
+ * members together: one launch per kernel over all subdomains of all
+ * members. */
+int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
+                      const double* const* f, const mrcm_bc* bcs, const mrcm_partition* parts,
+                      const mrcm_params* params, int device_ptrs, void* cuda_stream,
+                      mrcm_handle** out);
+
+/* Algorithm 1, Steps 1-4 (Sec. 2.1-2.2, Sec. 3): per subdomain, assemble and
+ * factor the hat-Omega_i operator, solve the N_i informed-space problems of
+ * Eq. (oversampling_problem), keep the restriction of each solution to
+ * Omega_i (Remark, Sec. 2.2) and its flux / face-pressure traces on Gamma_i,
+ * factor the Omega_i operator and solve the particular problem of Eqs.
+ * (111dbar)-(122dbar).  When alpha_smooth != alpha_basis it also factors the
+ * smoothing operator (Step 6). */
+int mrcm_build_basis(mrcm_handle* h);
+
+/* Algorithm 1, Step 5: assembles the interface rows of Eqs.
+ * (int_ujump)-(int_pjump) tested with all of M_H x V_H, solves them for the
+ * coefficients X (FP32 factorisation + FP64 iterative refinement to ir_tol),
+ * and assembles u = ubar + sum_j X_j Phi_j, p = pbar + sum_j X_j Psi_j
+ * (Eqs. (addu), (addp), (uhatphat)).  Pure-Neumann members are solved in the
+ * gauge X^0_0 = 0 and reported with zero-mean pressure.  Synchronises the
+ * stream (it reads the refinement residual). */
+int mrcm_solve_interface(mrcm_handle* h);
+
+/* Algorithm 1, Step 7 (Sec. 3, Eqs. (sm_1)-(sm_2)): n_steps smoothing steps.
+ * Colours c = sum_a (i_a mod 2) 2^a are visited in increasing order; each
+ * subdomain of a colour takes Robin data lambda = -beta u.n + pi on
+ * d hat-Omega_i \ d Omega from the current solution (beta with
+ * alpha_smooth), solves on hat-Omega_i with the factor kept from Step 1 or 6,
+ * and overwrites (u, p) on Omega_i.  smooth(a); smooth(b) == smooth(a + b). */
+int mrcm_smooth(mrcm_handle* h, int n_steps);
+
+/* Writes member `member`'s current solution: u_cellfaces [ncells][2 * dim]
+ * outward normal velocities, p_cells [ncells] (either may be NULL).
+ * device_ptrs 0: host buffers (the call synchronises); 1: device buffers. */
+int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells,
+                int device_ptrs);
+
+/* Counters of the last calls: ints[0] = number of subdomains (all members),
+ * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
+ * last solve, ints[3] = largest local refinement count of the last
+ * build/smooth call, ints[4] = local solves performed so far;
+ * dbl[0] = last interface relative residual.  Either pointer may be NULL. */
+int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl);
+
+int mrcm_destroy(mrcm_handle* h);
+
+/* Text of the last error of this handle ("" if none); valid until the next call. */
+const char* mrcm_last_error(const mrcm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCM_H */

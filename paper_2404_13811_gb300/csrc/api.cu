@@ -1,0 +1,747 @@
+// C ABI and host orchestration of the MRCM-OS library (include/mrcm.h).
+//
+// The host side plans the decomposition (subdomain boxes, oversampled boxes,
+// colours, interface numbering and slabs), owns every device allocation of a
+// handle, and issues the kernels on the caller's stream.  All arithmetic of
+// the method runs in the CUDA kernels of this library.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mrcm.h"
+#include "mrcm_internal.cuh"
+
+// launchers defined in the other translation units
+size_t local2d_smem(int prec, int nx, int ny, int nrhs);
+size_t smooth2d_smem(int prec, int nx, int ny);
+cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int bw,
+                           size_t smem, cudaStream_t s);
+cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems,
+                            size_t smem, cudaStream_t s);
+cudaError_t launch_assemble2d(const DevPtrs& P, const double* X, int nitems, int ncell_i_max,
+                              cudaStream_t s);
+cudaError_t launch_output(const MemberDev* dmem, int nmem, int member, const double* p, const double* u,
+                          long long off, long long nc, int nside, double* dmean, double* pout,
+                          double* uout, cudaStream_t s);
+
+cudaError_t if_assemble(const DevPtrs& P, const MethodDev& M, const IfPtrs& I, int nitems, int nrows,
+                        cudaStream_t s);
+cudaError_t bcr_fill(const IfPtrs& I, int nslab, cudaStream_t s);
+cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s);
+cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int first, cudaStream_t s);
+cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
+cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
+cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
+
+namespace {
+
+enum Stage { ST_CREATED = 0, ST_BASIS = 1, ST_SOLVED = 2 };
+
+struct JobClass {
+    int bw;
+    size_t smem;
+    int off, count;
+};
+
+struct Level {
+    int off, count;           // into the elimination array
+    float** dA;               // device pointer arrays for the batched inverse
+    float** dC;
+    int* dpiv;
+    int* dinfo;
+};
+
+}  // namespace
+
+struct mrcm_handle {
+    cudaStream_t stream = 0;
+    mrcm_params prm{};
+    int dim = 2;
+    int count = 0;
+    std::string err;
+    int stage = ST_CREATED;
+    // plan
+    std::vector<MemberDev> mem;
+    std::vector<SubDev> sub;
+    std::vector<SlabDev> slabs;
+    std::vector<ElimDev> elims;
+    std::vector<Level> levels;   // last level = roots
+    std::vector<JobClass> jclasses;
+    std::vector<int> colour_off; // colour c items: [colour_off[c], colour_off[c+1])
+    size_t smooth_smem = 0;
+    int nbasis_max = 0, ncell_i_max = 0, side_max = 0, npsi = 1;
+    long long ncells = 0;
+    int nif = 0, npad = 0, nmax_slab = 0;
+    size_t elim_smem = 0;
+    MethodDev mth{};
+    // device
+    MemberDev* d_mem = nullptr;
+    SubDev* d_sub = nullptr;
+    Job* d_jobs = nullptr;
+    int* d_colour_items = nullptr;
+    double *d_K = nullptr, *d_f = nullptr, *d_p = nullptr, *d_u = nullptr;
+    void* d_fac = nullptr;
+    double* d_dsc = nullptr;
+    double *d_Psi = nullptr, *d_Ug = nullptr, *d_pbar = nullptr, *d_ubg = nullptr, *d_mom = nullptr;
+    int* d_status = nullptr;
+    double* d_mean = nullptr;
+    DevPtrs P{};
+    // interface
+    IfPtrs I{};
+    SlabDev* d_slabs = nullptr;
+    ElimDev* d_elims = nullptr;
+    int* d_row_member = nullptr;
+    cublasHandle_t cublas = nullptr;
+    std::vector<void*> allocs;
+    // stats
+    int if_iters = 0;
+    double if_res = 0.0;
+    int loc_ir = 0;
+    long long local_solves = 0;
+};
+
+namespace {
+
+int fail(mrcm_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((h), MRCM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int dalloc(mrcm_handle* h, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+    if (e != cudaSuccess) return fail(h, MRCM_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return 0;
+}
+
+int check_inputs(mrcm_handle* h, const mrcm_grid* g, const mrcm_bc* bc, const mrcm_partition* pt,
+                 const mrcm_params* pr) {
+    if (!g || !bc || !pt || !pr) return fail(h, MRCM_ERR_BAD_INPUT, "null argument");
+    if (g->dim != 2 && g->dim != 3) return fail(h, MRCM_ERR_BAD_INPUT, "dim must be 2 or 3");
+    for (int a = 0; a < g->dim; ++a) {
+        if (g->n[a] <= 0 || !(g->h[a] > 0.0) || !std::isfinite(g->h[a]))
+            return fail(h, MRCM_ERR_BAD_INPUT, "grid sizes must be positive");
+        if (pt->sub[a] <= 0 || g->n[a] % pt->sub[a])
+            return fail(h, MRCM_ERR_BAD_INPUT, "subdomain size must divide the grid");
+        if (pt->overlap < 0 || 2 * pt->overlap >= pt->sub[a])
+            return fail(h, MRCM_ERR_BAD_INPUT, "need 0 <= 2*overlap < subdomain size");
+    }
+    for (int s = 0; s < 2 * g->dim; ++s)
+        if (bc->kind[s] != MRCM_NEUMANN && bc->kind[s] != MRCM_DIRICHLET)
+            return fail(h, MRCM_ERR_BAD_INPUT, "bad boundary kind");
+    if (pr->space != MRCM_P0 && pr->space != MRCM_P1) return fail(h, MRCM_ERR_BAD_INPUT, "bad space");
+    if (pr->precision != MRCM_FP64 && pr->precision != MRCM_MIXED)
+        return fail(h, MRCM_ERR_BAD_INPUT, "bad precision");
+    if (!(pr->alpha_basis > 0.0) || !(pr->alpha_smooth > 0.0))
+        return fail(h, MRCM_ERR_BAD_INPUT, "alpha must be positive");
+    if (pr->max_ir < 1) return fail(h, MRCM_ERR_BAD_INPUT, "max_ir must be >= 1");
+    return 0;
+}
+
+// -------------------------------------------------------------------------
+// planning
+// -------------------------------------------------------------------------
+int plan(mrcm_handle* h, const mrcm_grid* grids, const mrcm_bc* bcs, const mrcm_partition* parts) {
+    const int d = h->dim;
+    const int npsi = h->prm.space == MRCM_P0 ? 1 : (d == 2 ? 2 : 3);
+    h->npsi = npsi;
+    long long cell_off = 0;
+    int if_off = 0;
+    for (int m = 0; m < h->count; ++m) {
+        const mrcm_grid& g = grids[m];
+        const mrcm_bc& bc = bcs[m];
+        const mrcm_partition& pt = parts[m];
+        MemberDev md{};
+        md.dim = d;
+        long long nc = 1;
+        for (int a = 0; a < 3; ++a) {
+            md.n[a] = a < d ? g.n[a] : 1;
+            md.h[a] = a < d ? g.h[a] : 1.0;
+            md.sub[a] = a < d ? pt.sub[a] : 1;
+            md.M[a] = md.n[a] / md.sub[a];
+            md.Hw[a] = md.sub[a] * md.h[a];
+            nc *= md.n[a];
+        }
+        md.overlap = pt.overlap;
+        md.pure_neumann = 1;
+        for (int s = 0; s < 6; ++s) {
+            md.bc_kind[s] = s < 2 * d ? bc.kind[s] : MRCM_NEUMANN;
+            md.bc_val[s] = s < 2 * d ? bc.value[s] : 0.0;
+            if (s < 2 * d && bc.kind[s] == MRCM_DIRICHLET) md.pure_neumann = 0;
+        }
+        md.cell_off = cell_off;
+        md.sub0 = (int)h->sub.size();
+        md.nsub = md.M[0] * md.M[1] * md.M[2];
+        md.if0 = if_off;
+        if (md.nsub < 2) return fail(h, MRCM_ERR_BAD_INPUT, "need at least two subdomains");
+        for (int idx = 0; idx < md.nsub; ++idx) {
+            SubDev sd{};
+            sd.member = m;
+            int r = idx;
+            for (int a = 0; a < 3; ++a) {
+                sd.multi[a] = r % md.M[a];
+                r /= md.M[a];
+            }
+            sd.side_mask = 0;
+            sd.colour = 0;
+            for (int a = 0; a < 3; ++a) {
+                sd.lo[a] = sd.multi[a] * md.sub[a];
+                sd.hi[a] = sd.lo[a] + md.sub[a];
+                sd.loh[a] = a < d ? std::max(0, sd.lo[a] - pt.overlap) : 0;
+                sd.hih[a] = a < d ? std::min(md.n[a], sd.hi[a] + pt.overlap) : 1;
+                if (a < d) {
+                    if (sd.multi[a] > 0) sd.side_mask |= 1 << (2 * a);
+                    if (sd.multi[a] < md.M[a] - 1) sd.side_mask |= 1 << (2 * a + 1);
+                    sd.colour |= (sd.multi[a] & 1) << a;
+                }
+            }
+            int nsides = __builtin_popcount(sd.side_mask);
+            sd.nbasis = nsides * npsi;
+            sd.col0 = if_off;
+            if_off += sd.nbasis;
+            for (int s = 0; s < 6; ++s) {
+                sd.nbr[s] = -1;
+                if (sd.side_mask & (1 << s)) {
+                    int a = s >> 1;
+                    int stride = 1;
+                    for (int b = 0; b < a; ++b) stride *= md.M[b];
+                    sd.nbr[s] = md.sub0 + idx + ((s & 1) ? stride : -stride);
+                }
+            }
+            h->sub.push_back(sd);
+            h->nbasis_max = std::max(h->nbasis_max, sd.nbasis);
+            int nci = 1;
+            for (int a = 0; a < d; ++a) nci *= md.sub[a];
+            h->ncell_i_max = std::max(h->ncell_i_max, nci);
+            for (int a = 0; a < d; ++a) {
+                int face = 1;
+                for (int b = 0; b < d; ++b)
+                    if (b != a) face *= md.sub[b];
+                h->side_max = std::max(h->side_max, face);
+            }
+        }
+        md.nif = if_off - md.if0;
+        // interface slabs along the last axis
+        const int la = d - 1;
+        const int S = md.M[la];
+        const int per = md.nsub / S;
+        md.slab0 = (int)h->slabs.size();
+        md.nslab = S;
+        int ldc = 0;
+        for (int j = 0; j < S; ++j) {
+            SlabDev sl{};
+            sl.member = m;
+            sl.col0 = h->sub[md.sub0 + j * per].col0;
+            int n = 0;
+            for (int q = 0; q < per; ++q) n += h->sub[md.sub0 + j * per + q].nbasis;
+            sl.n = n;
+            sl.up = j + 1 < S ? md.slab0 + j + 1 : -1;
+            sl.dn = j > 0 ? md.slab0 + j - 1 : -1;
+            ldc = std::max(ldc, n);
+            h->slabs.push_back(sl);
+        }
+        for (int j = 0; j < S; ++j) h->slabs[md.slab0 + j].ldc = ldc;
+        h->mem.push_back(md);
+        cell_off += nc;
+    }
+    h->ncells = cell_off;
+    h->nif = if_off;
+    return 0;
+}
+
+// row (kind, side) of local row q of a subdomain, mirroring k_if_assemble
+void row_kind(const SubDev& sd, int d, int npsi, int q, int* kind, int* sid) {
+    *kind = -1;
+    for (int a = 0; a < d; ++a) {
+        int sh = 2 * a + 1;
+        if (sd.side_mask & (1 << sh)) {
+            if (q < npsi) { *kind = 0; *sid = sh; return; }
+            q -= npsi;
+        }
+    }
+    for (int a = 0; a < d; ++a) {
+        int sl = 2 * a;
+        if (sd.side_mask & (1 << sl)) {
+            if (q < npsi) { *kind = 1; *sid = sl; return; }
+            q -= npsi;
+        }
+    }
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------
+// creation
+// -------------------------------------------------------------------------
+static int create_impl(int count, const mrcm_grid* grids, const double* const* K, const double* const* f,
+                       const mrcm_bc* bcs, const mrcm_partition* parts, const mrcm_params* params,
+                       int device_ptrs, void* stream, mrcm_handle** out) {
+    if (!out) return MRCM_ERR_BAD_INPUT;
+    *out = nullptr;
+    mrcm_handle* h = new mrcm_handle();
+    *out = h;
+    if (count < 1 || !grids || !K || !f || !bcs || !parts || !params)
+        return fail(h, MRCM_ERR_BAD_INPUT, "bad arguments");
+    h->stream = (cudaStream_t)stream;
+    h->prm = *params;
+    h->count = count;
+    h->dim = grids[0].dim;
+    for (int m = 0; m < count; ++m) {
+        int rc = check_inputs(h, &grids[m], &bcs[m], &parts[m], params);
+        if (rc) return rc;
+        if (grids[m].dim != h->dim) return fail(h, MRCM_ERR_BAD_INPUT, "members must share dim");
+    }
+    if (h->dim != 2) return fail(h, MRCM_ERR_UNSUPPORTED, "3D subdomains are not available in this build");
+    int rc = plan(h, grids, bcs, parts);
+    if (rc) return rc;
+    for (int m = 0; m < count; ++m) {
+        const MemberDev& md = h->mem[m];
+        long long nc = (long long)md.n[0] * md.n[1] * md.n[2];
+        if (!K[m] || !f[m]) return fail(h, MRCM_ERR_BAD_INPUT, "null K or f");
+        if (!device_ptrs) {
+            for (long long c = 0; c < nc; ++c)
+                if (!(K[m][c] > 0.0) || !std::isfinite(K[m][c]) || !std::isfinite(f[m][c]))
+                    return fail(h, MRCM_ERR_BAD_INPUT, "K must be positive and finite, f finite");
+        }
+    }
+    const int d = h->dim;
+    const int prec = h->prm.precision;
+    const size_t tsz = prec == MRCM_FP64 ? sizeof(double) : sizeof(float);
+    h->mth.space = h->prm.space;
+    h->mth.npsi = h->npsi;
+    h->mth.prec = prec;
+    h->mth.alpha_b = h->prm.alpha_basis;
+    h->mth.alpha_s = h->prm.alpha_smooth;
+    h->mth.ir_tol = h->prm.ir_tol > 0 ? h->prm.ir_tol : 1e-12;
+    h->mth.max_ir = prec == MRCM_FP64 ? 1 : h->prm.max_ir;
+    h->mth.same_alpha = h->prm.alpha_basis == h->prm.alpha_smooth;
+
+    // jobs: basis, particular, smoothing factor
+    std::map<int, std::vector<Job>> byw;
+    std::map<int, size_t> smem_w;
+    size_t fac_stride = 0, dsc_stride = 0;
+    const int nitems = (int)h->sub.size();
+    for (int s = 0; s < nitems; ++s) {
+        const SubDev& sd = h->sub[s];
+        int bx = sd.hih[0] - sd.loh[0], by = sd.hih[1] - sd.loh[1];
+        int ix = sd.hi[0] - sd.lo[0], iy = sd.hi[1] - sd.lo[1];
+        if (bx > 32 || ix > 32)
+            return fail(h, MRCM_ERR_UNSUPPORTED, "2D boxes wider than 32 cells along x are not supported");
+        fac_stride = std::max(fac_stride, (size_t)bx * bx * by);
+        dsc_stride = std::max(dsc_stride, (size_t)bx * by);
+        auto add = [&](int type, int nx, int ny, int nrhs) {
+            int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
+            byw[bw].push_back(Job{s, type});
+            smem_w[bw] = std::max(smem_w[bw], local2d_smem(prec, nx, ny, std::max(nrhs, 1)));
+        };
+        add(JOB_BASIS, bx, by, sd.nbasis);
+        add(JOB_PART, ix, iy, 1);
+        if (!h->mth.same_alpha) add(JOB_SFACT, bx, by, 0);
+        h->smooth_smem = std::max(h->smooth_smem, smooth2d_smem(prec, bx, by));
+    }
+    std::vector<Job> jobs;
+    for (auto& kv : byw) {
+        JobClass jc{kv.first, smem_w[kv.first], (int)jobs.size(), (int)kv.second.size()};
+        if (jc.smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "subdomain box too large for shared memory");
+        h->jclasses.push_back(jc);
+        jobs.insert(jobs.end(), kv.second.begin(), kv.second.end());
+    }
+    // colours
+    std::vector<int> citems;
+    h->colour_off.assign((1 << d) + 1, 0);
+    for (int c = 0; c < (1 << d); ++c) {
+        h->colour_off[c] = (int)citems.size();
+        for (int s = 0; s < nitems; ++s)
+            if (h->sub[s].colour == c) citems.push_back(s);
+    }
+    h->colour_off[1 << d] = (int)citems.size();
+
+    // ---- device allocations ----
+    int e = 0;
+    const int nmem = (int)h->mem.size();
+    if ((e = dalloc(h, &h->d_mem, nmem))) return e;
+    if ((e = dalloc(h, &h->d_sub, nitems))) return e;
+    if ((e = dalloc(h, &h->d_jobs, jobs.size()))) return e;
+    if ((e = dalloc(h, &h->d_colour_items, citems.size()))) return e;
+    if ((e = dalloc(h, &h->d_K, h->ncells))) return e;
+    if ((e = dalloc(h, &h->d_f, h->ncells))) return e;
+    if ((e = dalloc(h, &h->d_p, h->ncells))) return e;
+    if ((e = dalloc(h, &h->d_u, h->ncells * 2 * d))) return e;
+    if ((e = dalloc(h, (char**)&h->d_fac, fac_stride * nitems * tsz))) return e;
+    if ((e = dalloc(h, &h->d_dsc, dsc_stride * nitems))) return e;
+    if ((e = dalloc(h, &h->d_Psi, (size_t)nitems * h->nbasis_max * h->ncell_i_max))) return e;
+    if ((e = dalloc(h, &h->d_Ug, (size_t)nitems * h->nbasis_max * MRCM_MAXSIDE * h->side_max))) return e;
+    if ((e = dalloc(h, &h->d_pbar, (size_t)nitems * h->ncell_i_max))) return e;
+    if ((e = dalloc(h, &h->d_ubg, (size_t)nitems * MRCM_MAXSIDE * h->side_max))) return e;
+    if ((e = dalloc(h, &h->d_mom, (size_t)nitems * (h->nbasis_max + 1) * MRCM_MAXSIDE * h->npsi * 2))) return e;
+    if ((e = dalloc(h, &h->d_status, 4))) return e;
+    if ((e = dalloc(h, &h->d_mean, nmem))) return e;
+    cudaStream_t st = h->stream;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_mem, h->mem.data(), sizeof(MemberDev) * nmem, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_sub, h->sub.data(), sizeof(SubDev) * nitems, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_colour_items, citems.data(), sizeof(int) * citems.size(),
+                                cudaMemcpyHostToDevice, st));
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int m = 0; m < count; ++m) {
+        const MemberDev& md = h->mem[m];
+        long long nc = (long long)md.n[0] * md.n[1] * md.n[2];
+        CUDA_TRY(h, cudaMemcpyAsync(h->d_K + md.cell_off, K[m], sizeof(double) * nc, kind, st));
+        CUDA_TRY(h, cudaMemcpyAsync(h->d_f + md.cell_off, f[m], sizeof(double) * nc, kind, st));
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->ncells, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_u, 0, sizeof(double) * h->ncells * 2 * d, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_mom, 0,
+                                sizeof(double) * nitems * (h->nbasis_max + 1) * MRCM_MAXSIDE * h->npsi * 2, st));
+
+    DevPtrs& P = h->P;
+    P.mem = h->d_mem;
+    P.sub = h->d_sub;
+    P.K = h->d_K;
+    P.f = h->d_f;
+    P.p = h->d_p;
+    P.u = h->d_u;
+    P.fac = h->d_fac;
+    P.fac_stride = (long long)fac_stride;
+    P.dsc = h->d_dsc;
+    P.dsc_stride = (long long)dsc_stride;
+    P.Psi = h->d_Psi;
+    P.Ug = h->d_Ug;
+    P.pbar = h->d_pbar;
+    P.ubg = h->d_ubg;
+    P.mom = h->d_mom;
+    P.nbasis_max = h->nbasis_max;
+    P.ncell_i_max = h->ncell_i_max;
+    P.side_max = h->side_max;
+    P.npsi = h->npsi;
+    P.status = h->d_status;
+
+    // ---- interface plan: slabs, row index lists, elimination levels ----
+    std::vector<int> idxpool;
+    long long offD = 0, offC = 0, offR = 0;
+    int npad = 0;
+    for (auto& sl : h->slabs) npad = std::max(npad, sl.n);
+    npad = (npad + 3) & ~3;
+    h->npad = npad;
+    h->nmax_slab = npad;
+    std::vector<int> row_member(h->nif);
+    for (auto& md : h->mem)
+        for (int r = md.if0; r < md.if0 + md.nif; ++r) row_member[r] = (int)(&md - &h->mem[0]);
+    size_t elim_smem = 0;
+    for (size_t j = 0; j < h->slabs.size(); ++j) {
+        SlabDev& sl = h->slabs[j];
+        const MemberDev& md = h->mem[sl.member];
+        const int la = d - 1;
+        std::vector<int> mrows, vrows, mpos(sl.n, -1), vpos(sl.n, -1);
+        for (int s = md.sub0; s < md.sub0 + md.nsub; ++s) {
+            const SubDev& sd = h->sub[s];
+            if (sd.col0 < sl.col0 || sd.col0 >= sl.col0 + sl.n) continue;
+            for (int q = 0; q < sd.nbasis; ++q) {
+                int kind, sid;
+                row_kind(sd, d, h->npsi, q, &kind, &sid);
+                int rr = sd.col0 + q - sl.col0;
+                if (kind == 0 && sid == 2 * la + 1) { mpos[rr] = (int)mrows.size(); mrows.push_back(rr); }
+                if (kind == 1 && sid == 2 * la) { vpos[rr] = (int)vrows.size(); vrows.push_back(rr); }
+            }
+        }
+        sl.nm = (int)mrows.size();
+        sl.nv = (int)vrows.size();
+        sl.offIdx = (long long)idxpool.size();
+        idxpool.insert(idxpool.end(), mrows.begin(), mrows.end());
+        idxpool.insert(idxpool.end(), vrows.begin(), vrows.end());
+        idxpool.insert(idxpool.end(), mpos.begin(), mpos.end());
+        idxpool.insert(idxpool.end(), vpos.begin(), vpos.end());
+        sl.offD = offD;
+        offD += (long long)npad * npad;
+        sl.offCup = offC;
+        sl.offCdn = offC + (long long)sl.nm * sl.ldc;
+        offC += (long long)(sl.nm + sl.nv) * sl.ldc;
+        sl.offRup = offR;
+        sl.offRdn = offR + (long long)sl.ldc * sl.n;
+        offR += 2LL * sl.ldc * sl.n;
+        sl.offPiv = (long long)j * npad;
+        size_t sm = sizeof(float) * 4 * (size_t)sl.ldc * sl.ldc;
+        elim_smem = std::max(elim_smem, std::min(sm, (size_t)200 * 1024));
+    }
+    // small-product scratch: bounded by the largest couplings
+    {
+        size_t need = 0;
+        for (auto& sl : h->slabs) {
+            size_t nmv = std::max(sl.nm, sl.nv);
+            need = std::max(need, sizeof(float) * 4 * nmv * nmv);
+        }
+        h->elim_smem = need;
+        if (need > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface coupling blocks too large");
+    }
+    // elimination levels over all members
+    int maxS = 0;
+    for (auto& md : h->mem) maxS = std::max(maxS, md.nslab);
+    for (int step = 1; step < maxS; step *= 2) {
+        Level L{};
+        L.off = (int)h->elims.size();
+        for (auto& md : h->mem) {
+            for (int j = step; j < md.nslab; j += 2 * step) {
+                ElimDev E{md.slab0 + j, md.slab0 + j - step, j + step < md.nslab ? md.slab0 + j + step : -1};
+                h->elims.push_back(E);
+            }
+        }
+        L.count = (int)h->elims.size() - L.off;
+        h->levels.push_back(L);
+    }
+    {
+        Level L{};
+        L.off = (int)h->elims.size();
+        for (auto& md : h->mem) h->elims.push_back(ElimDev{md.slab0, -1, -1});
+        L.count = (int)h->elims.size() - L.off;
+        h->levels.push_back(L);
+    }
+    const size_t nsl = h->slabs.size();
+    IfPtrs& I = h->I;
+    const int NB = h->nbasis_max;
+    I.NB = NB;
+    I.npad = npad;
+    if ((e = dalloc(h, &I.Gv, (size_t)h->nif * 2 * NB))) return e;
+    if ((e = dalloc(h, &I.Gc, (size_t)h->nif * 2))) return e;
+    if ((e = dalloc(h, &I.Gn, (size_t)h->nif * 2))) return e;
+    if ((e = dalloc(h, &I.rhs, h->nif))) return e;
+    if ((e = dalloc(h, &I.R, h->nif))) return e;
+    if ((e = dalloc(h, &I.Cs, h->nif))) return e;
+    if ((e = dalloc(h, &I.colmax, h->nif))) return e;
+    if ((e = dalloc(h, &I.x, h->nif))) return e;
+    if ((e = dalloc(h, &I.r, h->nif))) return e;
+    if ((e = dalloc(h, &I.bq, h->nif))) return e;
+    if ((e = dalloc(h, &I.D, (size_t)offD))) return e;
+    if ((e = dalloc(h, &I.Dinv, (size_t)offD))) return e;
+    if ((e = dalloc(h, &I.Cup, (size_t)offC))) return e;
+    I.Cdn = I.Cup;
+    if ((e = dalloc(h, &I.Rup, (size_t)offR))) return e;
+    I.Rdn = I.Rup;
+    if ((e = dalloc(h, &I.idx, idxpool.size()))) return e;
+    if ((e = dalloc(h, &I.rnorm, 2 * nmem))) return e;
+    if ((e = dalloc(h, &h->d_slabs, nsl))) return e;
+    if ((e = dalloc(h, &h->d_elims, h->elims.size()))) return e;
+    if ((e = dalloc(h, &h->d_row_member, h->nif))) return e;
+    I.slabs = h->d_slabs;
+    CUDA_TRY(h, cudaMemcpyAsync(I.idx, idxpool.data(), sizeof(int) * idxpool.size(), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_slabs, h->slabs.data(), sizeof(SlabDev) * nsl, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_elims, h->elims.data(), sizeof(ElimDev) * h->elims.size(),
+                                cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_row_member, row_member.data(), sizeof(int) * h->nif,
+                                cudaMemcpyHostToDevice, st));
+    // batched-inverse pointer arrays per level
+    for (auto& L : h->levels) {
+        std::vector<float*> A(L.count), C(L.count);
+        for (int q = 0; q < L.count; ++q) {
+            const SlabDev& sl = h->slabs[h->elims[L.off + q].j];
+            A[q] = I.D + sl.offD;
+            C[q] = I.Dinv + sl.offD;
+        }
+        if ((e = dalloc(h, &L.dA, L.count))) return e;
+        if ((e = dalloc(h, &L.dC, L.count))) return e;
+        if ((e = dalloc(h, &L.dpiv, (size_t)L.count * npad))) return e;
+        if ((e = dalloc(h, &L.dinfo, L.count))) return e;
+        CUDA_TRY(h, cudaMemcpyAsync(L.dA, A.data(), sizeof(float*) * L.count, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(h, cudaMemcpyAsync(L.dC, C.data(), sizeof(float*) * L.count, cudaMemcpyHostToDevice, st));
+    }
+    if (cublasCreate(&h->cublas) != CUBLAS_STATUS_SUCCESS) return fail(h, MRCM_ERR_CUDA, "cublasCreate failed");
+    cublasSetStream(h->cublas, st);
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return 0;
+}
+
+static int check_status(mrcm_handle* h) {
+    int st[4];
+    CUDA_TRY(h, cudaMemcpyAsync(st, h->d_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->loc_ir = std::max(h->loc_ir, st[1]);
+    if (st[0] & ST_NOT_SPD) return fail(h, MRCM_ERR_NOT_SPD, "non-positive pivot in a local factorisation (item " + std::to_string(st[2]) + ")");
+    if (st[0] & ST_NO_CONV) return fail(h, MRCM_ERR_NO_CONVERGENCE, "local iterative refinement did not reach ir_tol");
+    return 0;
+}
+
+extern "C" {
+
+int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
+                const mrcm_partition* part, const mrcm_params* params, int device_ptrs, void* cuda_stream,
+                mrcm_handle** out) {
+    const double* Ks[1] = {K};
+    const double* fs[1] = {f};
+    return create_impl(1, grid, Ks, fs, bc, part, params, device_ptrs, cuda_stream, out);
+}
+
+int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K, const double* const* f,
+                      const mrcm_bc* bcs, const mrcm_partition* parts, const mrcm_params* params,
+                      int device_ptrs, void* cuda_stream, mrcm_handle** out) {
+    return create_impl(count, grids, K, f, bcs, parts, params, device_ptrs, cuda_stream, out);
+}
+
+int mrcm_build_basis(mrcm_handle* h) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (h->stage != ST_CREATED) return fail(h, MRCM_ERR_STATE, "mrcm_build_basis must follow mrcm_create");
+    h->err.clear();
+    cudaStream_t st = h->stream;
+    for (auto& jc : h->jclasses) {
+        cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, st);
+        if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
+    }
+    int rc = check_status(h);
+    if (rc) return rc;
+    for (auto& sd : h->sub) h->local_solves += sd.nbasis + 1;
+    h->stage = ST_BASIS;
+    return 0;
+}
+
+int mrcm_solve_interface(mrcm_handle* h) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (h->stage != ST_BASIS) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must follow mrcm_build_basis");
+    h->err.clear();
+    cudaStream_t st = h->stream;
+    IfPtrs& I = h->I;
+    const int nitems = (int)h->sub.size();
+    const int nmem = (int)h->mem.size();
+    CUDA_TRY(h, if_assemble(h->P, h->mth, I, nitems, h->nif, st));
+    CUDA_TRY(h, bcr_fill(I, (int)h->slabs.size(), st));
+    // factorisation, level by level
+    for (size_t l = 0; l < h->levels.size(); ++l) {
+        Level& L = h->levels[l];
+        if (L.count == 0) continue;
+        if (cublasSgetrfBatched(h->cublas, h->npad, L.dA, h->npad, L.dpiv, L.dinfo, L.count) != CUBLAS_STATUS_SUCCESS)
+            return fail(h, MRCM_ERR_CUDA, "cublasSgetrfBatched failed");
+        if (cublasSgetriBatched(h->cublas, h->npad, (const float* const*)L.dA, h->npad, L.dpiv, L.dC, h->npad, L.dinfo,
+                                L.count) != CUBLAS_STATUS_SUCCESS)
+            return fail(h, MRCM_ERR_CUDA, "cublasSgetriBatched failed");
+        if (l + 1 < h->levels.size())
+            CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
+    }
+    // refinement
+    CUDA_TRY(h, cudaMemsetAsync(I.x, 0, sizeof(double) * h->nif, st));
+    std::vector<unsigned long long> nrm(2 * nmem);
+    const int nlev = (int)h->levels.size();
+    int it = 0;
+    double worst = 0.0;
+    const int max_it = std::max(8, h->prm.max_ir);
+    for (;; ++it) {
+        if (it == 0) CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * 2 * nmem, st));
+        else CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * nmem * 2, st));
+        // keep the rhs norms from the first pass: recompute each time (cheap)
+        CUDA_TRY(h, if_residual(I, h->d_row_member, h->nif, 1, st));
+        if (it > 0) {
+            CUDA_TRY(h, cudaMemcpyAsync(nrm.data(), I.rnorm, sizeof(unsigned long long) * 2 * nmem,
+                                        cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(h, cudaStreamSynchronize(st));
+            worst = 0.0;
+            for (int m = 0; m < nmem; ++m) {
+                double rn, bn;
+                std::memcpy(&rn, &nrm[2 * m], 8);
+                std::memcpy(&bn, &nrm[2 * m + 1], 8);
+                worst = std::max(worst, bn > 0 ? rn / bn : rn);
+            }
+            if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
+            if (worst <= h->mth.ir_tol || it >= max_it) break;
+        }
+        for (int l = 0; l < nlev; ++l) {
+            const Level& L = h->levels[l];
+            CUDA_TRY(h, bcr_fwd(I, h->d_elims + L.off, L.count, h->npad, st));
+        }
+        for (int l = nlev - 2; l >= 0; --l) {
+            const Level& L = h->levels[l];
+            CUDA_TRY(h, bcr_bwd(I, h->d_elims + L.off, L.count, h->npad, st));
+        }
+        CUDA_TRY(h, if_update(I, h->nif, st));
+    }
+    h->if_iters = it;
+    h->if_res = worst;
+    if (worst > h->mth.ir_tol * 1e3) return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled");
+    CUDA_TRY(h, launch_assemble2d(h->P, I.x, nitems, h->ncell_i_max, st));
+    h->stage = ST_SOLVED;
+    return 0;
+}
+
+int mrcm_smooth(mrcm_handle* h, int n_steps) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_smooth must follow mrcm_solve_interface");
+    if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
+    h->err.clear();
+    const int nc = 1 << h->dim;
+    for (int k = 0; k < n_steps; ++k) {
+        for (int c = 0; c < nc; ++c) {
+            int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
+            cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
+            if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
+        }
+    }
+    h->local_solves += (long long)n_steps * h->sub.size();
+    return check_status(h);
+}
+
+int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells, int device_ptrs) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "no solution yet");
+    if (member < 0 || member >= (int)h->mem.size()) return fail(h, MRCM_ERR_BAD_INPUT, "bad member");
+    const MemberDev& md = h->mem[member];
+    long long nc = (long long)md.n[0] * md.n[1] * md.n[2];
+    const int nside = 2 * h->dim;
+    cudaStream_t st = h->stream;
+    double *pd = p_cells, *ud = u_cellfaces;
+    double *tp = nullptr, *tu = nullptr;
+    if (!device_ptrs) {
+        if (p_cells) CUDA_TRY(h, cudaMallocAsync((void**)&tp, sizeof(double) * nc, st));
+        if (u_cellfaces) CUDA_TRY(h, cudaMallocAsync((void**)&tu, sizeof(double) * nc * nside, st));
+        pd = tp;
+        ud = tu;
+    }
+    CUDA_TRY(h, launch_output(h->d_mem, (int)h->mem.size(), member, h->d_p, h->d_u, md.cell_off, nc, nside,
+                              h->d_mean, pd, ud, st));
+    if (!device_ptrs) {
+        if (p_cells) CUDA_TRY(h, cudaMemcpyAsync(p_cells, tp, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+        if (u_cellfaces)
+            CUDA_TRY(h, cudaMemcpyAsync(u_cellfaces, tu, sizeof(double) * nc * nside, cudaMemcpyDeviceToHost, st));
+        if (tp) cudaFreeAsync(tp, st);
+        if (tu) cudaFreeAsync(tu, st);
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+    }
+    return 0;
+}
+
+int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    long long vals[5] = {(long long)h->sub.size(), h->nif, h->if_iters, h->loc_ir, h->local_solves};
+    for (int i = 0; i < nints && i < 5; ++i) ints[i] = (int)vals[i];
+    if (dbl && ndbl > 0) dbl[0] = h->if_res;
+    return 0;
+}
+
+int mrcm_destroy(mrcm_handle* h) {
+    if (!h) return 0;
+    if (!h->allocs.empty()) {
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+    }
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->cublas) cublasDestroy(h->cublas);
+    delete h;
+    return 0;
+}
+
+const char* mrcm_last_error(const mrcm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

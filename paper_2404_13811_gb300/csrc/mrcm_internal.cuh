@@ -1,0 +1,130 @@
+// Internal structures shared by the host orchestrator and the kernels of the
+// MRCM-OS library (see include/mrcm.h for the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MRCM_MAXD 3
+#define MRCM_MAXSIDE 6
+
+// Per problem (ensemble member) data visible to kernels.
+struct MemberDev {
+    int dim;
+    int n[3];
+    double h[3];
+    int bc_kind[6];
+    double bc_val[6];
+    int sub[3];
+    int overlap;
+    int M[3];          // subdomains per axis
+    long long cell_off;  // first cell of this member in the concatenated cell arrays
+    int sub0, nsub;    // work items (subdomains) of this member
+    int if0, nif;      // interface unknowns of this member
+    int pure_neumann;
+    double Hw[3];      // subdomain width per axis (H in beta = alpha H / K_H)
+    int slab0, nslab;  // interface slabs of this member
+};
+
+// Per subdomain (work item) data.
+struct SubDev {
+    int member;
+    int multi[3];
+    int lo[3], hi[3];      // Omega_i (cells, hi exclusive)
+    int loh[3], hih[3];    // hat-Omega_i
+    int side_mask;         // bit sid set when side sid of Omega_i is on Gamma_i
+    int nbasis;            // N_i
+    int col0;              // first interface unknown (== first owned row)
+    int colour;
+    int nbr[6];            // neighbour work item across each side (-1 on the domain boundary)
+    int slab;              // global slab id
+    int slab_pos;          // offset of this subdomain's unknowns inside its slab
+};
+
+// Interface slab (block row/column of the block-tridiagonal interface
+// system, one layer of subdomains along the last axis).
+struct SlabDev {
+    int member;
+    int n;          // unknowns (= rows) in the slab
+    int col0;       // first global unknown
+    int nm, nv;     // rows coupled to the next / previous slab
+    int up, dn;     // original neighbour slabs (-1 if none)
+    long long offD, offCup, offCdn, offRup, offRdn, offPiv, offIdx; // storage offsets
+    int ldc;        // leading dimension of the coupling blocks (max slab size of the member)
+};
+
+// One block-cyclic-reduction elimination: slab `j` eliminated with current
+// neighbours jm (below) and jp (above, -1 when none).
+struct ElimDev {
+    int j, jm, jp;
+};
+
+enum JobType { JOB_BASIS = 0, JOB_PART = 1, JOB_SFACT = 2 };
+
+struct Job {
+    int item;
+    int type;
+};
+
+struct DevPtrs {
+    const MemberDev* mem;
+    const SubDev* sub;
+    const double* K;
+    const double* f;
+    double* p;           // state pressure [ncells total]
+    double* u;           // state velocities [ncells total][2*dim]
+    // factors kept for smoothing
+    void* fac;           // T elements
+    long long fac_stride;
+    double* dsc;         // Jacobi scaling of the smoothing operator (mixed form)
+    long long dsc_stride;
+    // basis data
+    double* Psi;         // [item][nbasis_max][ncell_i_max]
+    double* Ug;          // [item][nbasis_max][2d][side_max]
+    double* pbar;        // [item][ncell_i_max]
+    double* ubg;         // [item][2d][side_max]
+    double* mom;         // [item][nbasis_max+1][2d][npsi][2]  (flux, pressure moments)
+    int nbasis_max, ncell_i_max, side_max, npsi;
+    int* status;         // [0] error bits, [1] max local refinement steps, [2] bad item
+};
+
+struct MethodDev {
+    int space, npsi, prec;
+    double alpha_b, alpha_s;
+    double ir_tol;
+    int max_ir;
+    int same_alpha;
+};
+
+
+// Device pointers of the interface system.
+struct IfPtrs {
+    double* Gv;    // [row][2][NB] FP64 row entries (owner block, neighbour block)
+    int* Gc;       // [row][2] first column of each block
+    int* Gn;       // [row][2] column count of each block
+    double* rhs;   // [row]
+    double* R;     // row scale
+    double* Cs;    // column scale
+    unsigned long long* colmax;
+    double* x;     // FP64 solution
+    double* r;     // FP64 residual
+    float* bq;     // FP32 right-hand side / solution (global unknown order)
+    float* D;      // slab diagonal blocks (column-major, npad x npad)
+    float* Dinv;   // their inverses
+    float* Cup;    // coupling rows to the slab above (pool shared with Cdn)
+    float* Cdn;
+    float* Rup;    // couplings into an eliminated slab, saved (pool shared with Rdn)
+    float* Rdn;
+    int* idx;      // row index lists per slab
+    const SlabDev* slabs;
+    unsigned long long* rnorm;   // [2 * nmember]: residual max, rhs max (bit patterns)
+    int NB;
+    int npad;
+};
+
+// status bits
+#define ST_NOT_SPD 1
+#define ST_NO_CONV 2
+#define ST_SINGULAR 4
+#define ST_BAD 8
+
+static inline __host__ __device__ int side_axis(int sid) { return sid >> 1; }

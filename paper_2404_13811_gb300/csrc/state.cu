@@ -1,0 +1,107 @@
+// Assembly of the MRCM-O solution from the interface coefficients and the
+// kept basis data (Eqs. (addu), (addp), (uhatphat); Algorithm 1, Step 5), and
+// output of the current solution.
+#include "mrcm_internal.cuh"
+
+__device__ __forceinline__ double harm_t(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// One CTA per subdomain: p = pbar + sum_k X_k Psi_k on Omega_i, Gamma_i
+// velocities ubar + sum_k X_k U_k, interior faces from the assembled
+// pressure (the same face law holds for every term of the superposition),
+// physical faces from the boundary data.
+__global__ void k_assemble2d(DevPtrs P, const double* __restrict__ X) {
+    extern __shared__ double ps[];
+    const int item = blockIdx.x;
+    const SubDev sd = P.sub[item];
+    const MemberDev& md = P.mem[sd.member];
+    const int nIx = sd.hi[0] - sd.lo[0], nIy = sd.hi[1] - sd.lo[1];
+    const int n = nIx * nIy;
+    const double* xs = X + sd.col0;
+    const double* Psi = P.Psi + (size_t)item * P.nbasis_max * P.ncell_i_max;
+    const double* pb = P.pbar + (size_t)item * P.ncell_i_max;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double v = pb[c];
+        for (int k = 0; k < sd.nbasis; ++k) v += xs[k] * Psi[(size_t)k * P.ncell_i_max + c];
+        ps[c] = v;
+    }
+    __syncthreads();
+    const double* K = P.K + md.cell_off;
+    double* pw = P.p + md.cell_off;
+    double* uw = P.u + md.cell_off * 4;
+    const double hx = md.h[0], hy = md.h[1];
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int i = c % nIx, j = c / nIx;
+        const int gx = sd.lo[0] + i, gy = sd.lo[1] + j;
+        const long long g = gx + (long long)md.n[0] * gy;
+        const double pc = ps[c];
+        const double kc = K[g];
+        pw[g] = pc;
+        for (int sid = 0; sid < 4; ++sid) {
+            const int a = sid >> 1;
+            const bool hi = sid & 1;
+            const int li = a == 0 ? i : j;
+            const int lext = a == 0 ? nIx : nIy;
+            const bool edge = hi ? (li == lext - 1) : (li == 0);
+            const double area = a == 0 ? hy : hx;
+            const double h = a == 0 ? hx : hy;
+            double uo;
+            if (!edge) {
+                const int cn = c + (a == 0 ? (hi ? 1 : -1) : (hi ? nIx : -nIx));
+                const long long gn = g + (a == 0 ? (hi ? 1 : -1) : (hi ? md.n[0] : -md.n[0]));
+                const double T = area * 2.0 * kc * K[gn] / (h * (kc + K[gn]));
+                uo = T * (pc - ps[cn]) / area;
+            } else if (sd.side_mask & (1 << sid)) {
+                const int e = a == 0 ? j : i;
+                double v = P.ubg[((size_t)item * MRCM_MAXSIDE + sid) * P.side_max + e];
+                for (int k = 0; k < sd.nbasis; ++k)
+                    v += xs[k] * P.Ug[(((size_t)item * P.nbasis_max + k) * MRCM_MAXSIDE + sid) * P.side_max + e];
+                uo = v;
+            } else if (md.bc_kind[sid] == 1) {
+                const double T = 2.0 * area * kc / h;
+                uo = T * (pc - md.bc_val[sid]) / area;
+            } else {
+                uo = md.bc_val[sid];
+            }
+            uw[g * 4 + sid] = uo;
+        }
+    }
+}
+
+// Deterministic per-member mean of the pressure (one CTA per member).
+__global__ void k_member_mean(const MemberDev* mem, const double* p, double* mean) {
+    __shared__ double red[256];
+    const MemberDev& md = mem[blockIdx.x];
+    long long nc = (long long)md.n[0] * md.n[1] * (md.dim == 3 ? md.n[2] : 1);
+    double s = 0.0;
+    for (long long c = threadIdx.x; c < nc; c += blockDim.x) s += p[md.cell_off + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[blockIdx.x] = md.pure_neumann ? red[0] / (double)nc : 0.0;
+}
+
+__global__ void k_output(const double* p, const double* u, long long off, long long nc, int nside,
+                         const double* mean, double* pout, double* uout) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    if (pout) pout[c] = p[off + c] - mean[0];
+    if (uout)
+        for (int s = 0; s < nside; ++s) uout[c * nside + s] = u[(off + c) * nside + s];
+}
+
+cudaError_t launch_assemble2d(const DevPtrs& P, const double* X, int nitems, int ncell_i_max,
+                              cudaStream_t s) {
+    k_assemble2d<<<nitems, 256, sizeof(double) * ncell_i_max, s>>>(P, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output(const MemberDev* dmem, int nmem, int member, const double* p, const double* u,
+                          long long off, long long nc, int nside, double* dmean, double* pout,
+                          double* uout, cudaStream_t s) {
+    k_member_mean<<<nmem, 256, 0, s>>>(dmem, p, dmean);
+    k_output<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(p, u, off, nc, nside, dmean + member, pout, uout);
+    return cudaGetLastError();
+}

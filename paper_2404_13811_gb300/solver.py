@@ -1,0 +1,107 @@
+"""Python front end of libmrcm.so: one object per handle.
+
+Device memory for inputs/outputs and the CUDA stream come from PyTorch;
+every step of the method runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class MRCM:
+    """MRCM-OS solver for one problem or an ensemble of problems.
+
+    problems: one object (or a list) with attributes dim, n, h, K, f,
+    bc_kind, bc_value (see ``inputs.Problem``); partitions: matching
+    (sub, overlap) objects; params: space, alpha_basis, alpha_smooth.
+    precision: "fp64" or "mixed".  K / f may be numpy arrays (copied from the
+    host) or CUDA tensors (copied on the device)."""
+
+    def __init__(self, problems, partitions, space=1, alpha_basis=1.0, alpha_smooth=1.0,
+                 precision="fp64", ir_tol=1e-12, max_ir=8, stream=None, device_inputs=False):
+        import torch
+        single = not isinstance(problems, (list, tuple))
+        self.problems = [problems] if single else list(problems)
+        parts = [partitions] * len(self.problems) if not isinstance(partitions, (list, tuple)) \
+            else list(partitions)
+        self.dim = self.problems[0].dim
+        prec = L.MRCM_FP64 if precision == "fp64" else L.MRCM_MIXED
+        self.params = L.make_params(space, alpha_basis, alpha_smooth, prec, ir_tol, max_ir)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        grids, bcs, pts, Ks, fs = [], [], [], [], []
+        self._keep = []
+        for pr, pt in zip(self.problems, parts):
+            g, b, p = L.make_structs(pr.dim, pr.n, pr.h, pr.bc_kind, pr.bc_value, pt.sub, pt.overlap)
+            grids.append(g)
+            bcs.append(b)
+            pts.append(p)
+            if device_inputs:
+                Kt = torch.as_tensor(np.ascontiguousarray(pr.K, dtype=np.float64)).cuda()
+                ft = torch.as_tensor(np.ascontiguousarray(pr.f, dtype=np.float64)).cuda()
+                self._keep += [Kt, ft]
+                Ks.append(Kt.data_ptr())
+                fs.append(ft.data_ptr())
+            else:
+                Kh = np.ascontiguousarray(pr.K, dtype=np.float64)
+                fh = np.ascontiguousarray(pr.f, dtype=np.float64)
+                self._keep += [Kh, fh]
+                Ks.append(Kh.ctypes.data)
+                fs.append(fh.ctypes.data)
+        sp = _stream_ptr(self.stream)
+        if len(self.problems) == 1:
+            self.h = L.mrcm_create(grids[0], Ks[0], fs[0], bcs[0], pts[0], self.params,
+                                   int(device_inputs), sp)
+        else:
+            self.h = L.mrcm_create_batch(grids, Ks, fs, bcs, pts, self.params, int(device_inputs), sp)
+        self._keep = []
+
+    def build_basis(self):
+        L.mrcm_build_basis(self.h)
+
+    def solve_interface(self):
+        L.mrcm_solve_interface(self.h)
+
+    def smooth(self, n_steps):
+        L.mrcm_smooth(self.h, n_steps)
+
+    def fluxes(self, member=0, device=False):
+        """(p [ncells], u [ncells, 2d]) of one member, x-fastest cell order."""
+        pr = self.problems[member]
+        nc = int(np.prod(pr.n))
+        if device:
+            import torch
+            p = torch.empty(nc, dtype=torch.float64, device="cuda")
+            u = torch.empty((nc, 2 * pr.dim), dtype=torch.float64, device="cuda")
+        else:
+            p = np.empty(nc)
+            u = np.empty((nc, 2 * pr.dim))
+        L.mrcm_fluxes(self.h, member, u, p)
+        return p, u
+
+    def stats(self):
+        return L.mrcm_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            L.mrcm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, n_smooth):
+        self.build_basis()
+        self.solve_interface()
+        if n_smooth:
+            self.smooth(n_smooth)

@@ -5,7 +5,8 @@
  *
  * Call order (enforced; an out-of-order call returns MRCM_ERR_STATE):
  *   mrcm_create / mrcm_create_batch
- *   mrcm_build_basis       Algorithm 1, Steps 1-4 (and 6 when alpha_smooth != alpha_basis)
+ *   mrcm_build_basis       Algorithm 1, Steps 1-4 (and 6 when alpha_smooth != alpha_basis);
+ *                          calling it again restarts the pipeline from the inputs
  *   mrcm_solve_interface   Algorithm 1, Step 5
  *   mrcm_smooth            Algorithm 1, Step 7 (any number of calls; additive in n_steps)
  *   mrcm_fluxes            read the current solution (any time after mrcm_solve_interface)
@@ -130,7 +131,7 @@ int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
  * factor the Omega_i operator and solve the particular problem of Eqs.
  * (111dbar)-(122dbar).  When alpha_smooth != alpha_basis it also factors the
  * smoothing operator (Step 6). */
-int mrcm_build_basis(mrcm_handle* h);
+int mrcm_build_basis(mrcm_handle* h);   /* any stage; restarts the pipeline */
 
 /* Algorithm 1, Step 5: assembles the interface rows of Eqs.
  * (int_ujump)-(int_pjump) tested with all of M_H x V_H, solves them for the
@@ -161,6 +162,21 @@ int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells
  * build/smooth call, ints[4] = local solves performed so far;
  * dbl[0] = last interface relative residual.  Either pointer may be NULL. */
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl);
+
+/* Device-time profiling of the calls above.  enable = 1 starts recording a
+ * pair of CUDA events around every kernel group on the handle's stream (and
+ * clears what was recorded); enable = 0 stops.  Phases:
+ *   0 local basis / particular / smoothing-factor kernels (mrcm_build_basis)
+ *   1 interface assembly, equilibration and slab factorisation
+ *   2 interface refinement sweeps (residual, forward, backward, update)
+ *   3 assembly of the MRCM-O solution
+ *   4 smoothing colour phases (mrcm_smooth)
+ * mrcm_timings synchronises the stream and writes, for each of the first n
+ * phases, the summed device time in ms (ms[i]) and the number of kernel
+ * launches of this library in that phase (launches[i]); either pointer may be
+ * NULL.  Launches are counted whether or not profiling is enabled. */
+int mrcm_profile(mrcm_handle* h, int enable);
+int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n);
 
 int mrcm_destroy(mrcm_handle* h);
 

@@ -41,7 +41,9 @@ class mrcm_params(C.Structure):
 
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
-           "mrcm_smooth", "mrcm_fluxes", "mrcm_stats", "mrcm_destroy", "mrcm_last_error"]
+           "mrcm_smooth", "mrcm_fluxes", "mrcm_stats", "mrcm_profile", "mrcm_timings",
+           "mrcm_destroy", "mrcm_last_error"]
+PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth"]
 
 _lib = None
 
@@ -72,6 +74,8 @@ def load(path=LIBPATH):
     lib.mrcm_smooth.argtypes = [vp, C.c_int]
     lib.mrcm_fluxes.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.mrcm_stats.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double), C.c_int]
+    lib.mrcm_profile.argtypes = [vp, C.c_int]
+    lib.mrcm_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
     lib.mrcm_last_error.argtypes = [vp]
     lib.mrcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -190,6 +194,20 @@ def mrcm_stats(h):
     _check(lib, h, lib.mrcm_stats(h, ints, 5, dbl, 1))
     return {"subdomains": ints[0], "interface_unknowns": ints[1], "interface_ir_steps": ints[2],
             "local_ir_steps": ints[3], "local_solves": ints[4], "interface_residual": dbl[0]}
+
+
+def mrcm_profile(h, enable):
+    lib = load()
+    _check(lib, h, lib.mrcm_profile(h, int(enable)))
+
+
+def mrcm_timings(h):
+    """{phase: (device ms, launches)} since the last mrcm_profile call."""
+    lib = load()
+    ms = (C.c_double * 5)()
+    ln = (C.c_longlong * 5)()
+    _check(lib, h, lib.mrcm_timings(h, ms, ln, 5))
+    return {PHASES[i]: (ms[i], ln[i]) for i in range(5)}
 
 
 def mrcm_destroy(h):

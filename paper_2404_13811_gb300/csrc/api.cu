@@ -100,6 +100,12 @@ struct mrcm_handle {
     int* d_row_member = nullptr;
     cublasHandle_t cublas = nullptr;
     std::vector<void*> allocs;
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
+    long long launches[5] = {0, 0, 0, 0, 0};
     // stats
     int if_iters = 0;
     double if_res = 0.0;
@@ -120,6 +126,37 @@ int fail(mrcm_handle* h, int code, const std::string& msg) {
         if (e_ != cudaSuccess)                                                                \
             return fail((h), MRCM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+cudaEvent_t take_event(mrcm_handle* h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// Records device time of one phase when profiling is on.
+struct Phase {
+    mrcm_handle* h;
+    int ph;
+    cudaEvent_t a = nullptr;
+    Phase(mrcm_handle* hh, int p) : h(hh), ph(p) {
+        if (h->prof) {
+            a = take_event(h);
+            if (a) cudaEventRecord(a, h->stream);
+        }
+    }
+    ~Phase() {
+        if (h->prof && a) {
+            cudaEvent_t b = take_event(h);
+            if (b) {
+                cudaEventRecord(b, h->stream);
+                h->ev_rec.push_back({ph, {a, b}});
+            }
+        }
+    }
+};
 
 template <typename T>
 int dalloc(mrcm_handle* h, T** p, size_t count) {
@@ -596,12 +633,16 @@ int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
 
 int mrcm_build_basis(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
-    if (h->stage != ST_CREATED) return fail(h, MRCM_ERR_STATE, "mrcm_build_basis must follow mrcm_create");
     h->err.clear();
+    h->stage = ST_CREATED;
     cudaStream_t st = h->stream;
-    for (auto& jc : h->jclasses) {
-        cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, st);
-        if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
+    {
+        Phase ph(h, 0);
+        for (auto& jc : h->jclasses) {
+            cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, st);
+            if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
+            h->launches[0] += 1;
+        }
     }
     int rc = check_status(h);
     if (rc) return rc;
@@ -618,8 +659,10 @@ int mrcm_solve_interface(mrcm_handle* h) {
     IfPtrs& I = h->I;
     const int nitems = (int)h->sub.size();
     const int nmem = (int)h->mem.size();
+    Phase* ph1 = new Phase(h, 1);
     CUDA_TRY(h, if_assemble(h->P, h->mth, I, nitems, h->nif, st));
     CUDA_TRY(h, bcr_fill(I, (int)h->slabs.size(), st));
+    h->launches[1] += 4;
     // factorisation, level by level
     for (size_t l = 0; l < h->levels.size(); ++l) {
         Level& L = h->levels[l];
@@ -629,9 +672,12 @@ int mrcm_solve_interface(mrcm_handle* h) {
         if (cublasSgetriBatched(h->cublas, h->npad, (const float* const*)L.dA, h->npad, L.dpiv, L.dC, h->npad, L.dinfo,
                                 L.count) != CUBLAS_STATUS_SUCCESS)
             return fail(h, MRCM_ERR_CUDA, "cublasSgetriBatched failed");
-        if (l + 1 < h->levels.size())
+        if (l + 1 < h->levels.size()) {
             CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
+            h->launches[1] += 1;
+        }
     }
+    delete ph1;
     // refinement
     CUDA_TRY(h, cudaMemsetAsync(I.x, 0, sizeof(double) * h->nif, st));
     std::vector<unsigned long long> nrm(2 * nmem);
@@ -639,11 +685,13 @@ int mrcm_solve_interface(mrcm_handle* h) {
     int it = 0;
     double worst = 0.0;
     const int max_it = std::max(8, h->prm.max_ir);
+    Phase* ph2 = new Phase(h, 2);
     for (;; ++it) {
         if (it == 0) CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * 2 * nmem, st));
         else CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * nmem * 2, st));
         // keep the rhs norms from the first pass: recompute each time (cheap)
         CUDA_TRY(h, if_residual(I, h->d_row_member, h->nif, 1, st));
+        h->launches[2] += 1;
         if (it > 0) {
             CUDA_TRY(h, cudaMemcpyAsync(nrm.data(), I.rnorm, sizeof(unsigned long long) * 2 * nmem,
                                         cudaMemcpyDeviceToHost, st));
@@ -655,23 +703,34 @@ int mrcm_solve_interface(mrcm_handle* h) {
                 std::memcpy(&bn, &nrm[2 * m + 1], 8);
                 worst = std::max(worst, bn > 0 ? rn / bn : rn);
             }
-            if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
+            if (!std::isfinite(worst)) {
+                delete ph2;
+                return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
+            }
             if (worst <= h->mth.ir_tol || it >= max_it) break;
         }
         for (int l = 0; l < nlev; ++l) {
             const Level& L = h->levels[l];
             CUDA_TRY(h, bcr_fwd(I, h->d_elims + L.off, L.count, h->npad, st));
+            h->launches[2] += 1;
         }
         for (int l = nlev - 2; l >= 0; --l) {
             const Level& L = h->levels[l];
             CUDA_TRY(h, bcr_bwd(I, h->d_elims + L.off, L.count, h->npad, st));
+            h->launches[2] += 1;
         }
         CUDA_TRY(h, if_update(I, h->nif, st));
+        h->launches[2] += 1;
     }
+    delete ph2;
     h->if_iters = it;
     h->if_res = worst;
     if (worst > h->mth.ir_tol * 1e3) return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled");
-    CUDA_TRY(h, launch_assemble2d(h->P, I.x, nitems, h->ncell_i_max, st));
+    {
+        Phase ph3(h, 3);
+        CUDA_TRY(h, launch_assemble2d(h->P, I.x, nitems, h->ncell_i_max, st));
+        h->launches[3] += 1;
+    }
     h->stage = ST_SOLVED;
     return 0;
 }
@@ -682,11 +741,15 @@ int mrcm_smooth(mrcm_handle* h, int n_steps) {
     if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
     h->err.clear();
     const int nc = 1 << h->dim;
-    for (int k = 0; k < n_steps; ++k) {
-        for (int c = 0; c < nc; ++c) {
-            int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
-            cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
-            if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
+    {
+        Phase ph4(h, 4);
+        for (int k = 0; k < n_steps; ++k) {
+            for (int c = 0; c < nc; ++c) {
+                int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
+                cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
+                if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
+                h->launches[4] += 1;
+            }
         }
     }
     h->local_solves += (long long)n_steps * h->sub.size();
@@ -730,6 +793,32 @@ int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl
     return 0;
 }
 
+int mrcm_profile(mrcm_handle* h, int enable) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->prof = enable != 0;
+    h->ev_rec.clear();
+    h->ev_used = 0;
+    for (auto& v : h->launches) v = 0;
+    return 0;
+}
+
+int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (auto& r : h->ev_rec) {
+        float t = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&t, r.second.first, r.second.second));
+        if (r.first >= 0 && r.first < 5) acc[r.first] += t;
+    }
+    for (int i = 0; i < n && i < 5; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = h->launches[i];
+    }
+    return 0;
+}
+
 int mrcm_destroy(mrcm_handle* h) {
     if (!h) return 0;
     if (!h->allocs.empty()) {
@@ -737,6 +826,7 @@ int mrcm_destroy(mrcm_handle* h) {
         else cudaDeviceSynchronize();
     }
     for (void* p : h->allocs) cudaFree(p);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->cublas) cublasDestroy(h->cublas);
     delete h;
     return 0;

@@ -89,6 +89,12 @@ class MRCM:
     def stats(self):
         return L.mrcm_stats(self.h)
 
+    def profile(self, enable=True):
+        L.mrcm_profile(self.h, enable)
+
+    def timings(self):
+        return L.mrcm_timings(self.h)
+
     def close(self):
         if getattr(self, "h", None) is not None:
             L.mrcm_destroy(self.h)

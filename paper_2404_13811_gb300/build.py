@@ -60,7 +60,7 @@ def build(verbose=False, extra=()):
         objs = list(ex.map(lambda s: _compile(s, list(extra), verbose), srcs))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcublas"]
+    cmd = [nvcc(), "-shared", "-o", LIB] + objs + ARCH
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

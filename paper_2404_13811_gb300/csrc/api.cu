@@ -4,7 +4,6 @@
 // colours, interface numbering and slabs), owns every device allocation of a
 // handle, and issues the kernels on the caller's stream.  All arithmetic of
 // the method runs in the CUDA kernels of this library.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +38,7 @@ cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int f
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
+cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
 
 namespace {
 
@@ -52,10 +52,6 @@ struct JobClass {
 
 struct Level {
     int off, count;           // into the elimination array
-    float** dA;               // device pointer arrays for the batched inverse
-    float** dC;
-    int* dpiv;
-    int* dinfo;
 };
 
 }  // namespace
@@ -98,7 +94,6 @@ struct mrcm_handle {
     SlabDev* d_slabs = nullptr;
     ElimDev* d_elims = nullptr;
     int* d_row_member = nullptr;
-    cublasHandle_t cublas = nullptr;
     std::vector<void*> allocs;
     // profiling
     bool prof = false;
@@ -584,23 +579,6 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
                                 cudaMemcpyHostToDevice, st));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_row_member, row_member.data(), sizeof(int) * h->nif,
                                 cudaMemcpyHostToDevice, st));
-    // batched-inverse pointer arrays per level
-    for (auto& L : h->levels) {
-        std::vector<float*> A(L.count), C(L.count);
-        for (int q = 0; q < L.count; ++q) {
-            const SlabDev& sl = h->slabs[h->elims[L.off + q].j];
-            A[q] = I.D + sl.offD;
-            C[q] = I.Dinv + sl.offD;
-        }
-        if ((e = dalloc(h, &L.dA, L.count))) return e;
-        if ((e = dalloc(h, &L.dC, L.count))) return e;
-        if ((e = dalloc(h, &L.dpiv, (size_t)L.count * npad))) return e;
-        if ((e = dalloc(h, &L.dinfo, L.count))) return e;
-        CUDA_TRY(h, cudaMemcpyAsync(L.dA, A.data(), sizeof(float*) * L.count, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(h, cudaMemcpyAsync(L.dC, C.data(), sizeof(float*) * L.count, cudaMemcpyHostToDevice, st));
-    }
-    if (cublasCreate(&h->cublas) != CUBLAS_STATUS_SUCCESS) return fail(h, MRCM_ERR_CUDA, "cublasCreate failed");
-    cublasSetStream(h->cublas, st);
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return 0;
 }
@@ -667,11 +645,8 @@ int mrcm_solve_interface(mrcm_handle* h) {
     for (size_t l = 0; l < h->levels.size(); ++l) {
         Level& L = h->levels[l];
         if (L.count == 0) continue;
-        if (cublasSgetrfBatched(h->cublas, h->npad, L.dA, h->npad, L.dpiv, L.dinfo, L.count) != CUBLAS_STATUS_SUCCESS)
-            return fail(h, MRCM_ERR_CUDA, "cublasSgetrfBatched failed");
-        if (cublasSgetriBatched(h->cublas, h->npad, (const float* const*)L.dA, h->npad, L.dpiv, L.dC, h->npad, L.dinfo,
-                                L.count) != CUBLAS_STATUS_SUCCESS)
-            return fail(h, MRCM_ERR_CUDA, "cublasSgetriBatched failed");
+        CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
+        h->launches[1] += 1;
         if (l + 1 < h->levels.size()) {
             CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
             h->launches[1] += 1;
@@ -684,6 +659,7 @@ int mrcm_solve_interface(mrcm_handle* h) {
     const int nlev = (int)h->levels.size();
     int it = 0;
     double worst = 0.0;
+    std::string hist;
     const int max_it = std::max(8, h->prm.max_ir);
     Phase* ph2 = new Phase(h, 2);
     for (;; ++it) {
@@ -703,6 +679,9 @@ int mrcm_solve_interface(mrcm_handle* h) {
                 std::memcpy(&bn, &nrm[2 * m + 1], 8);
                 worst = std::max(worst, bn > 0 ? rn / bn : rn);
             }
+            char buf[32];
+            snprintf(buf, sizeof(buf), " %.2e", worst);
+            hist += buf;
             if (!std::isfinite(worst)) {
                 delete ph2;
                 return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
@@ -725,7 +704,8 @@ int mrcm_solve_interface(mrcm_handle* h) {
     delete ph2;
     h->if_iters = it;
     h->if_res = worst;
-    if (worst > h->mth.ir_tol * 1e3) return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled");
+    if (worst > h->mth.ir_tol * 1e3)
+        return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled; residuals:" + hist);
     {
         Phase ph3(h, 3);
         CUDA_TRY(h, launch_assemble2d(h->P, I.x, nitems, h->ncell_i_max, st));
@@ -827,7 +807,6 @@ int mrcm_destroy(mrcm_handle* h) {
     }
     for (void* p : h->allocs) cudaFree(p);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
-    if (h->cublas) cublasDestroy(h->cublas);
     delete h;
     return 0;
 }

@@ -11,6 +11,7 @@
 // FP32 after row/column equilibration, with FP64 residuals of the unscaled
 // rows driving iterative refinement to ir_tol.
 #include "mrcm_internal.cuh"
+#include <algorithm>
 
 
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
@@ -401,4 +402,298 @@ cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
     k_if_update<<<(ncols + 255) / 256, 256, 0, s>>>(I, ncols);
     return cudaGetLastError();
+}
+
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
+constexpr int GJ_NB = 32;   // panel width
+constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
+constexpr int GJ_THREADS = 512;
+
+// ---------------------------------------------------------------------------
+// Slab inverse through a blocked LU factorisation with partial pivoting
+// (FP32, column-major np x np, in place in D, inverse written to Dinv).
+// Phase 1 (cluster-synchronised per panel of GJ_NB columns): every CTA of
+// the cluster factors the panel redundantly in shared memory, the owner
+// writes it back, and each CTA applies the interchanges to the columns it
+// owns, forms their U12 rows and updates their trailing part.
+// Phase 2 (independent per CTA): the columns of the inverse owned by a CTA
+// are solved from P A = L U: column j = U^-1 L^-1 e_{q(j)}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / GJ_CL;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int np = I.npad;
+    const int npan = (np + GJ_NB - 1) / GJ_NB;
+    const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
+    extern __shared__ __align__(16) float lsm[];
+    float* Ps = lsm;                           // [c][r], GJ_NB * np
+    float* Xs = Ps + GJ_NB * np;               // [jj][r], GJ_NB * np
+    float* Upy = Xs + GJ_NB * np;              // [c][jj], GJ_NB * ncmax
+    int* piv = (int*)(Upy + GJ_NB * ncmax);    // np
+    int* ownc = piv + np;                      // ncmax
+    int* qpos = ownc + ncmax;                  // np: position of the unit entry of P e_j
+    __shared__ float redv[32];
+    __shared__ int redi[32];
+    __shared__ int nown;
+    const bool active = e < nel;
+    float* A = nullptr;
+    float* Ainv = nullptr;
+    if (active) {
+        const SlabDev S = I.slabs[el[e].j];
+        A = I.D + S.offD;
+        Ainv = I.Dinv + S.offD;
+    }
+    if (tid == 0) {
+        int c = 0;
+        for (int q = rank; q < npan; q += GJ_CL)
+            for (int j = q * GJ_NB; j < min(np, (q + 1) * GJ_NB); ++j) ownc[c++] = j;
+        nown = c;
+    }
+    bool singular = false;
+    // ---------------- phase 1: P A = L U ----------------
+    for (int q = 0; q < npan; ++q) {
+        __threadfence();
+        cluster.sync();
+        const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
+        if (active)
+            for (int t = tid; t < b * (np - k0); t += nt) {
+                int c = t / (np - k0), r = k0 + t % (np - k0);
+                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
+            }
+        cluster.sync();
+        if (!active) continue;
+        for (int c = 0; c < b; ++c) {
+            const int r0 = k0 + c;
+            float best = -1.f;
+            int bi = r0;
+            for (int r = r0 + tid; r < np; r += nt) {
+                float v = fabsf(Ps[c * np + r]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int o = 16; o; o >>= 1) {
+                float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if ((tid & 31) == 0) { redv[tid >> 5] = best; redi[tid >> 5] = bi; }
+            __syncthreads();
+            if (tid < 32) {
+                float v = tid < (nt >> 5) ? redv[tid] : -1.f;
+                int ii = tid < (nt >> 5) ? redi[tid] : 0x7fffffff;
+                for (int o = 16; o; o >>= 1) {
+                    float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+                    if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
+                }
+                if (tid == 0) piv[r0] = ii;
+            }
+            __syncthreads();
+            const int p = piv[r0];
+            if (p != r0)
+                for (int cc = tid; cc < b; cc += nt) {
+                    float t0 = Ps[cc * np + r0];
+                    Ps[cc * np + r0] = Ps[cc * np + p];
+                    Ps[cc * np + p] = t0;
+                }
+            __syncthreads();
+            float a = Ps[c * np + r0];
+            if (a == 0.f) { singular = true; a = 1e-30f; }
+            const float ia = (float)(1.0 / (double)a);
+            for (int r = r0 + 1 + tid; r < np; r += nt) Ps[c * np + r] *= ia;
+            __syncthreads();
+            for (int t = tid; t < (b - c - 1) * (np - r0 - 1); t += nt) {
+                int cc = c + 1 + t / (np - r0 - 1), r = r0 + 1 + t % (np - r0 - 1);
+                Ps[cc * np + r] -= Ps[c * np + r] * Ps[cc * np + r0];
+            }
+            __syncthreads();
+        }
+        if (q % GJ_CL == rank)
+            for (int t = tid; t < b * (np - k0); t += nt) {
+                int c = t / (np - k0), r = k0 + t % (np - k0);
+                A[(size_t)(k0 + c) * np + r] = Ps[c * np + r];
+            }
+        const int no = nown;
+        // interchanges on every owned column outside the panel
+        for (int jj = tid; jj < no; jj += nt) {
+            const int j = ownc[jj];
+            if (j >= k0 && j < k0 + b) continue;
+            float* col = A + (size_t)j * np;
+            for (int c = 0; c < b; ++c) {
+                int p = piv[k0 + c];
+                if (p != k0 + c) { float t0 = col[k0 + c]; col[k0 + c] = col[p]; col[p] = t0; }
+            }
+        }
+        __syncthreads();
+        // U12 = L11^-1 A12 for owned trailing columns (one thread per column)
+        for (int jj = tid; jj < no; jj += nt) {
+            const int j = ownc[jj];
+            if (j < k0 + b) continue;
+            float* col = A + (size_t)j * np;
+            float x[GJ_NB];
+#pragma unroll
+            for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? col[k0 + c] : 0.f;
+#pragma unroll
+            for (int c = 0; c < GJ_NB; ++c)
+#pragma unroll
+                for (int c2 = c + 1; c2 < GJ_NB; ++c2)
+                    if (c2 < b) x[c2] -= Ps[c * np + k0 + c2] * x[c];
+#pragma unroll
+            for (int c = 0; c < GJ_NB; ++c)
+                if (c < b) {
+                    col[k0 + c] = x[c];
+                    Upy[c * ncmax + jj] = x[c];
+                }
+        }
+        __syncthreads();
+        // trailing update A22 -= L21 U12 over owned trailing columns
+        const int r1 = k0 + b;
+        if (r1 < np) {
+            const int ntr = (np - r1) / 4, ntc = (no + 3) / 4;
+            for (int t = tid; t < ntr * ntc; t += nt) {
+                const int r = r1 + (t % ntr) * 4, jj0 = (t / ntr) * 4;
+                float acc[4][4];
+                int jcol[4];
+                bool skip[4];
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    int jj = jj0 + y;
+                    jcol[y] = jj < no ? ownc[jj] : -1;
+                    skip[y] = jcol[y] < r1;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) acc[x][y] = skip[y] ? 0.f : A[(size_t)jcol[y] * np + r + x];
+                }
+                for (int c = 0; c < b; ++c) {
+                    const float4 s4 = *reinterpret_cast<const float4*>(&Ps[c * np + r]);
+                    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                    float av[4];
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) av[y] = skip[y] ? 0.f : Upy[c * ncmax + jj0 + y];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] -= sv[x] * av[y];
+                }
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                    if (!skip[y])
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) A[(size_t)jcol[y] * np + r + x] = acc[x][y];
+            }
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    cluster.sync();
+    if (!active) return;
+    // ---------------- phase 2: owned columns of the inverse ----------------
+    if (tid == 0) {
+        // rowperm[i] = original row at position i; qpos[j] = position of original row j
+        int* rowperm = (int*)Upy;
+        for (int i = 0; i < np; ++i) rowperm[i] = i;
+        for (int c = 0; c < np; ++c) {
+            int p = piv[c], t0 = rowperm[c];
+            rowperm[c] = rowperm[p];
+            rowperm[p] = t0;
+        }
+        for (int i = 0; i < np; ++i) qpos[rowperm[i]] = i;
+    }
+    __syncthreads();
+    const int no = nown;
+    for (int j0 = 0; j0 < no; j0 += GJ_NB) {
+        const int nb = min(GJ_NB, no - j0);
+        for (int t = tid; t < GJ_NB * np; t += nt) {
+            int jj = t / np, r = t % np;
+            Xs[t] = (jj < nb && r == qpos[ownc[j0 + jj]]) ? 1.f : 0.f;
+        }
+        __syncthreads();
+        // forward with unit L, panel by panel
+        for (int q = 0; q < npan; ++q) {
+            const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
+            for (int t = tid; t < b * (np - k0); t += nt) {
+                int c = t / (np - k0), r = k0 + t % (np - k0);
+                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
+            }
+            __syncthreads();
+            for (int jj = tid; jj < nb; jj += nt) {
+                float* xc = Xs + jj * np;
+                for (int c = 0; c < b; ++c) {
+                    const float xv = xc[k0 + c];
+                    for (int c2 = c + 1; c2 < b; ++c2) xc[k0 + c2] -= Ps[c * np + k0 + c2] * xv;
+                }
+            }
+            __syncthreads();
+            const int r1 = k0 + b;
+            for (int t = tid; t < (np - r1) * nb; t += nt) {
+                int jj = t / (np - r1), r = r1 + t % (np - r1);
+                float* xc = Xs + jj * np;
+                float acc = xc[r];
+                for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * xc[k0 + c];
+                xc[r] = acc;
+            }
+            __syncthreads();
+        }
+        // backward with U, panel by panel from the last
+        for (int q = npan - 1; q >= 0; --q) {
+            const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
+            for (int t = tid; t < b * (k0 + b); t += nt) {
+                int c = t / (k0 + b), r = t % (k0 + b);
+                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
+            }
+            __syncthreads();
+            for (int jj = tid; jj < nb; jj += nt) {
+                float* xc = Xs + jj * np;
+                for (int c = b - 1; c >= 0; --c) {
+                    const float xv = xc[k0 + c] / Ps[c * np + k0 + c];
+                    xc[k0 + c] = xv;
+                    for (int c2 = 0; c2 < c; ++c2) xc[k0 + c2] -= Ps[c * np + k0 + c2] * xv;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < k0 * nb; t += nt) {
+                int jj = t / k0, r = t % k0;
+                float* xc = Xs + jj * np;
+                float acc = xc[r];
+                for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * xc[k0 + c];
+                xc[r] = acc;
+            }
+            __syncthreads();
+        }
+        for (int t = tid; t < nb * np; t += nt) {
+            int jj = t / np, r = t % np;
+            Ainv[(size_t)ownc[j0 + jj] * np + r] = Xs[jj * np + r];
+        }
+        __syncthreads();
+    }
+    if (singular && tid == 0) atomicOr(status, ST_SINGULAR);
+}
+
+size_t lu_smem(int np) {
+    int npan = (np + GJ_NB - 1) / GJ_NB;
+    int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
+    size_t ncm = std::max((size_t)GJ_NB * ncmax, (size_t)np);
+    return sizeof(float) * (2 * (size_t)GJ_NB * np + ncm) + sizeof(int) * ((size_t)np + ncmax + np) + 16;
+}
+
+cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
+    if (nel == 0) return cudaSuccess;
+    size_t smem = lu_smem(I.npad);
+    cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nel * GJ_CL);
+    cfg.blockDim = dim3(GJ_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = GJ_CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_lu_inverse, I, el, nel, status);
 }

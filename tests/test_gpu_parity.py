@@ -128,8 +128,16 @@ def test_call_order_enforced():
     with pytest.raises(L.MrcmError):
         s.smooth(1)
     s.build_basis()
+    s.solve_interface()
+    s.smooth(1)
+    p1, u1 = s.fluxes()
+    s.build_basis()          # restarts the pipeline
     with pytest.raises(L.MrcmError):
-        s.build_basis()
+        s.smooth(1)
+    s.solve_interface()
+    s.smooth(1)
+    p2, u2 = s.fluxes()
+    assert np.array_equal(p1, p2) and np.array_equal(u1, u2)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

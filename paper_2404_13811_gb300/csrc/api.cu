@@ -26,6 +26,8 @@ cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* ite
                             size_t smem, cudaStream_t s);
 cudaError_t launch_assemble2d(const DevPtrs& P, const double* X, int nitems, int ncell_i_max,
                               cudaStream_t s);
+cudaError_t launch_faces(const MemberDev* dmem, int nmem, long long maxcells, const double* K, double* Tf,
+                         double* hk, double* wh, cudaStream_t s);
 cudaError_t launch_output(const MemberDev* dmem, int nmem, int member, const double* p, const double* u,
                           long long off, long long nc, int nside, double* dmean, double* pout,
                           double* uout, cudaStream_t s);
@@ -39,6 +41,7 @@ cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
+size_t elim_smem_bytes(int nmv, int nmax);
 
 namespace {
 
@@ -83,6 +86,7 @@ struct mrcm_handle {
     Job* d_jobs = nullptr;
     int* d_colour_items = nullptr;
     double *d_K = nullptr, *d_f = nullptr, *d_p = nullptr, *d_u = nullptr;
+    double *d_Tf = nullptr, *d_hk = nullptr, *d_wh = nullptr;
     void* d_fac = nullptr;
     double* d_dsc = nullptr;
     double *d_Psi = nullptr, *d_Ug = nullptr, *d_pbar = nullptr, *d_ubg = nullptr, *d_mom = nullptr;
@@ -377,7 +381,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         int ix = sd.hi[0] - sd.lo[0], iy = sd.hi[1] - sd.lo[1];
         if (bx > 32 || ix > 32)
             return fail(h, MRCM_ERR_UNSUPPORTED, "2D boxes wider than 32 cells along x are not supported");
-        fac_stride = std::max(fac_stride, (size_t)bx * bx * by);
+        fac_stride = std::max(fac_stride, ((size_t)bx * bx * by + 3) & ~size_t(3));  // 16-byte aligned slots
         dsc_stride = std::max(dsc_stride, (size_t)bx * by);
         auto add = [&](int type, int nx, int ny, int nrhs) {
             int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
@@ -417,6 +421,9 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     if ((e = dalloc(h, &h->d_f, h->ncells))) return e;
     if ((e = dalloc(h, &h->d_p, h->ncells))) return e;
     if ((e = dalloc(h, &h->d_u, h->ncells * 2 * d))) return e;
+    if ((e = dalloc(h, &h->d_Tf, h->ncells * 3))) return e;
+    if ((e = dalloc(h, &h->d_hk, h->ncells * 3))) return e;
+    if ((e = dalloc(h, &h->d_wh, h->ncells * 3))) return e;
     if ((e = dalloc(h, (char**)&h->d_fac, fac_stride * nitems * tsz))) return e;
     if ((e = dalloc(h, &h->d_dsc, dsc_stride * nitems))) return e;
     if ((e = dalloc(h, &h->d_Psi, (size_t)nitems * h->nbasis_max * h->ncell_i_max))) return e;
@@ -439,6 +446,11 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         CUDA_TRY(h, cudaMemcpyAsync(h->d_K + md.cell_off, K[m], sizeof(double) * nc, kind, st));
         CUDA_TRY(h, cudaMemcpyAsync(h->d_f + md.cell_off, f[m], sizeof(double) * nc, kind, st));
     }
+    {
+        long long maxc = 0;
+        for (auto& md : h->mem) maxc = std::max(maxc, (long long)md.n[0] * md.n[1] * md.n[2]);
+        CUDA_TRY(h, launch_faces(h->d_mem, nmem, maxc, h->d_K, h->d_Tf, h->d_hk, h->d_wh, st));
+    }
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->ncells, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_u, 0, sizeof(double) * h->ncells * 2 * d, st));
@@ -450,6 +462,9 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     P.sub = h->d_sub;
     P.K = h->d_K;
     P.f = h->d_f;
+    P.Tf = h->d_Tf;
+    P.hk = h->d_hk;
+    P.wh = h->d_wh;
     P.p = h->d_p;
     P.u = h->d_u;
     P.fac = h->d_fac;
@@ -478,7 +493,6 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     std::vector<int> row_member(h->nif);
     for (auto& md : h->mem)
         for (int r = md.if0; r < md.if0 + md.nif; ++r) row_member[r] = (int)(&md - &h->mem[0]);
-    size_t elim_smem = 0;
     for (size_t j = 0; j < h->slabs.size(); ++j) {
         SlabDev& sl = h->slabs[j];
         const MemberDev& md = h->mem[sl.member];
@@ -511,18 +525,13 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         sl.offRdn = offR + (long long)sl.ldc * sl.n;
         offR += 2LL * sl.ldc * sl.n;
         sl.offPiv = (long long)j * npad;
-        size_t sm = sizeof(float) * 4 * (size_t)sl.ldc * sl.ldc;
-        elim_smem = std::max(elim_smem, std::min(sm, (size_t)200 * 1024));
     }
-    // small-product scratch: bounded by the largest couplings
+    // Schur-update scratch: bounded by the largest couplings
     {
-        size_t need = 0;
-        for (auto& sl : h->slabs) {
-            size_t nmv = std::max(sl.nm, sl.nv);
-            need = std::max(need, sizeof(float) * 4 * nmv * nmv);
-        }
-        h->elim_smem = need;
-        if (need > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface coupling blocks too large");
+        size_t nmv = 0;
+        for (auto& sl : h->slabs) nmv = std::max(nmv, (size_t)std::max(sl.nm, sl.nv));
+        h->elim_smem = elim_smem_bytes((int)nmv, npad);
+        if (h->elim_smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface coupling blocks too large");
     }
     // elimination levels over all members
     int maxS = 0;
@@ -572,6 +581,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     if ((e = dalloc(h, &h->d_slabs, nsl))) return e;
     if ((e = dalloc(h, &h->d_elims, h->elims.size()))) return e;
     if ((e = dalloc(h, &h->d_row_member, h->nif))) return e;
+
     I.slabs = h->d_slabs;
     CUDA_TRY(h, cudaMemcpyAsync(I.idx, idxpool.data(), sizeof(int) * idxpool.size(), cudaMemcpyHostToDevice, st));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_slabs, h->slabs.data(), sizeof(SlabDev) * nsl, cudaMemcpyHostToDevice, st));
@@ -590,6 +600,7 @@ static int check_status(mrcm_handle* h) {
     h->loc_ir = std::max(h->loc_ir, st[1]);
     if (st[0] & ST_NOT_SPD) return fail(h, MRCM_ERR_NOT_SPD, "non-positive pivot in a local factorisation (item " + std::to_string(st[2]) + ")");
     if (st[0] & ST_NO_CONV) return fail(h, MRCM_ERR_NO_CONVERGENCE, "local iterative refinement did not reach ir_tol");
+    if (st[0] & ST_BAD) return fail(h, MRCM_ERR_CUDA, "a staged copy did not complete in time");
     return 0;
 }
 

@@ -12,6 +12,13 @@
 // rows driving iterative refinement to ir_tol.
 #include "mrcm_internal.cuh"
 #include <algorithm>
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
+constexpr int GJ_NB = 32;   // panel width
+constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
+constexpr int GJ_THREADS = 512;
+
 
 
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
@@ -149,103 +156,141 @@ __global__ void k_bcr_fill(IfPtrs I, int nslab) {
 // where Qv / Qm are the columns of Dinv_j at j's pressure / flux coupling
 // rows, Rup = Cup_jm (saved) and Rdn = Cdn_jp (saved).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_bcr_elim(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float sm[];
-    const int e = blockIdx.x;
-    if (e >= nel) return;
-    const ElimDev E = el[e];
-    const SlabDev Sj = I.slabs[E.j];
-    const SlabDev Sm = I.slabs[E.jm];
+// Rows x Q product: out[m][n] = sum_k L[m][k] Dinv[k][col(n)] for m < M, n < N,
+// with L row-major (ld n_j) in global memory and the columns of Dinv picked
+// by `cols`.  K is staged through shared memory in chunks of 32.
+__device__ void rows_times_cols(const float* L, int M, int K, const float* Dinv, int np, const int* cols, int N,
+                                float* out, float* stL, float* stQ) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < M * N; t += nt) out[t] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int kb = min(32, K - k0);
+        __syncthreads();
+        for (int t = tid; t < M * 32; t += nt) {
+            const int m = t >> 5, k = t & 31;
+            stL[t] = k < kb ? __ldcg(&L[(size_t)m * K + k0 + k]) : 0.f;
+        }
+        for (int t = tid; t < N * 32; t += nt) {
+            const int n = t >> 5, k = t & 31;
+            stQ[k * N + n] = k < kb ? Dinv[(size_t)cols[n] * np + k0 + k] : 0.f;
+        }
+        __syncthreads();
+        for (int t = tid; t < M * N; t += nt) {
+            const int m = t / N, n = t - (t / N) * N;
+            float acc = out[t];
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) acc += stL[m * 32 + k] * stQ[k * N + n];
+            out[t] = acc;
+        }
+    }
+    __syncthreads();
+}
+
+// out rows r of a target: tgt(r, c) op= sum_q A[r][q] C[q][c] for c < ncol,
+// with C row-major (ld ldc) in global memory staged in shared memory.
+template <bool ACCUM_INTO_D>
+__device__ void apply_coupling(const float* Asm, int M, int M2, const float* Cg, int ldc, int ncol, float* Csm,
+                               float* D, int np, const int* rows, float* Cout, int ldout, int nclear) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < M2 * ncol; t += nt) {
+        const int q = t / ncol, c = t - (t / ncol) * ncol;
+        Csm[t] = Cg[(size_t)q * ldc + c];
+    }
+    __syncthreads();
+    for (int t = tid; t < M * ncol; t += nt) {
+        const int r = t / ncol, c = t - (t / ncol) * ncol;
+        float acc = 0.f;
+        for (int q = 0; q < M2; ++q) acc += Asm[r * M2 + q] * Csm[q * ncol + c];
+        if (ACCUM_INTO_D) D[(size_t)c * np + rows[r]] -= acc;
+        else Cout[(size_t)r * ldout + c] = -acc;
+    }
+    if (!ACCUM_INTO_D)
+        for (int t = tid; t < M * (nclear - ncol); t += nt) {
+            const int r = t / (nclear - ncol), c = ncol + t % (nclear - ncol);
+            Cout[(size_t)r * ldout + c] = 0.f;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// One block-cyclic-reduction elimination of slab j (after Dinv_j is known),
+// one cluster of 4 CTAs.  With Qv / Qm the columns of Dinv_j at j's
+// pressure / flux coupling rows, Rup = Cup_jm and Rdn = Cdn_jp (saved first):
+//   rank 0: D_jm[mrows] -= (Rup Qv) Cdn_j      rank 1: Cup_jm <- -(Rup Qm) Cup_j
+//   rank 2: D_jp[vrows] -= (Rdn Qm) Cup_j      rank 3: Cdn_jp <- -(Rdn Qv) Cdn_j
+// ---------------------------------------------------------------------------
+constexpr int EL_THREADS = 512;
+
+__global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev* el, int nel) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / GJ_CL;
+    extern __shared__ __align__(16) float esm[];
+    const bool active = e < nel;
+    ElimDev E{0, 0, -1};
+    SlabDev Sj{}, Sm{}, Sp{};
+    if (active) {
+        E = el[e];
+        Sj = I.slabs[E.j];
+        Sm = I.slabs[E.jm];
+        if (E.jp >= 0) Sp = I.slabs[E.jp];
+    }
     const int np = I.npad;
-    const float* Dinv = I.Dinv + Sj.offD;  // column-major np x np
-    const int* mrows_j = I.idx + Sj.offIdx;
-    const int* vrows_j = mrows_j + Sj.nm;
-    // save couplings into j
+    const int tid = threadIdx.x, nt = blockDim.x;
     float* Rup = I.Rup + Sj.offRup;  // nm_jm x n_j
     float* Rdn = I.Rdn + Sj.offRdn;  // nv_jp x n_j
-    const float* CupM = I.Cup + Sm.offCup;
-    for (int t = threadIdx.x; t < Sm.nm * Sj.n; t += blockDim.x) {
-        int r = t / Sj.n, c = t % Sj.n;
-        Rup[t] = CupM[(size_t)r * Sm.ldc + c];
-    }
-    SlabDev Sp;
-    if (E.jp >= 0) {
-        Sp = I.slabs[E.jp];
-        const float* CdnP = I.Cdn + Sp.offCdn;
-        for (int t = threadIdx.x; t < Sp.nv * Sj.n; t += blockDim.x) {
-            int r = t / Sj.n, c = t % Sj.n;
-            Rdn[t] = CdnP[(size_t)r * Sp.ldc + c];
+    if (active) {
+        // save the couplings into j (split over the cluster)
+        const float* CupM = I.Cup + Sm.offCup;
+        for (int t = tid + rank * nt; t < Sm.nm * Sj.n; t += nt * GJ_CL) {
+            const int r = t / Sj.n, c = t - (t / Sj.n) * Sj.n;
+            Rup[t] = CupM[(size_t)r * Sm.ldc + c];
+        }
+        if (E.jp >= 0) {
+            const float* CdnP = I.Cdn + Sp.offCdn;
+            for (int t = tid + rank * nt; t < Sp.nv * Sj.n; t += nt * GJ_CL) {
+                const int r = t / Sj.n, c = t - (t / Sj.n) * Sj.n;
+                Rdn[t] = CdnP[(size_t)r * Sp.ldc + c];
+            }
         }
     }
-    __syncthreads();
-    // small products: A1 = Rup Qv (nm_jm x nv_j), A2 = Rup Qm (nm_jm x nm_j)
-    const int nvj = Sj.nv, nmj = (E.jp >= 0) ? Sj.nm : 0;
-    float* A1 = sm;                      // Sm.nm * nvj
-    float* A2 = A1 + Sm.nm * nvj;        // Sm.nm * nmj
-    float* A3 = A2 + Sm.nm * nmj;        // Sp.nv * nmj
-    float* A4 = A3 + (E.jp >= 0 ? Sp.nv * nmj : 0);  // Sp.nv * nvj
-    for (int t = threadIdx.x; t < Sm.nm * (nvj + nmj); t += blockDim.x) {
-        int r = t / (nvj + nmj), q = t % (nvj + nmj);
-        int col = q < nvj ? vrows_j[q] : mrows_j[q - nvj];
-        const float* Q = Dinv + (size_t)col * np;  // column col of Dinv
-        const float* rr = Rup + (size_t)r * Sj.n;
-        float acc = 0.f;
-        for (int c = 0; c < Sj.n; ++c) acc += rr[c] * Q[c];
-        if (q < nvj) A1[r * nvj + q] = acc;
-        else A2[r * nmj + (q - nvj)] = acc;
-    }
-    if (E.jp >= 0) {
-        for (int t = threadIdx.x; t < Sp.nv * (nvj + nmj); t += blockDim.x) {
-            int r = t / (nvj + nmj), q = t % (nvj + nmj);
-            int col = q < nmj ? mrows_j[q] : vrows_j[q - nmj];
-            const float* Q = Dinv + (size_t)col * np;
-            const float* rr = Rdn + (size_t)r * Sj.n;
-            float acc = 0.f;
-            for (int c = 0; c < Sj.n; ++c) acc += rr[c] * Q[c];
-            if (q < nmj) A3[r * nmj + q] = acc;
-            else A4[r * nvj + (q - nmj)] = acc;
-        }
-    }
-    __syncthreads();
+    __threadfence();
+    cluster.sync();
+    if (!active) return;
+    const float* Dinv = I.Dinv + Sj.offD;
+    const int* mrows_j = I.idx + Sj.offIdx;
+    const int* vrows_j = mrows_j + Sj.nm;
     const float* Cdn_j = I.Cdn + Sj.offCdn;  // nv_j x ldc, columns = jm unknowns
     const float* Cup_j = I.Cup + Sj.offCup;  // nm_j x ldc, columns = jp unknowns
-    // jm: diagonal rows and the new upper coupling
-    {
-        float* Dm = I.D + Sm.offD;
-        float* CupM_w = I.Cup + Sm.offCup;
-        const int* mrows_m = I.idx + Sm.offIdx;
-        for (int t = threadIdx.x; t < Sm.nm * Sm.n; t += blockDim.x) {
-            int r = t / Sm.n, c = t % Sm.n;
-            float acc = 0.f;
-            for (int q = 0; q < nvj; ++q) acc += A1[r * nvj + q] * Cdn_j[(size_t)q * Sj.ldc + c];
-            Dm[(size_t)c * np + mrows_m[r]] -= acc;
-        }
-        const int njp = (E.jp >= 0) ? Sp.n : 0;
-        for (int t = threadIdx.x; t < Sm.nm * Sm.ldc; t += blockDim.x) {
-            int r = t / Sm.ldc, c = t % Sm.ldc;
-            float acc = 0.f;
-            if (c < njp)
-                for (int q = 0; q < nmj; ++q) acc -= A2[r * nmj + q] * Cup_j[(size_t)q * Sj.ldc + c];
-            CupM_w[t] = acc;
-        }
+    const bool up = rank < 2;
+    if (!up && E.jp < 0) return;
+    const float* Lrows = up ? Rup : Rdn;
+    const int M = up ? Sm.nm : Sp.nv;
+    const bool useQv = (rank == 0 || rank == 3);
+    const int N = useQv ? Sj.nv : Sj.nm;
+    const int* cols = useQv ? vrows_j : mrows_j;
+    if (rank == 1 && E.jp < 0) {
+        // no slab above any more: jm loses its upper coupling
+        float* CupM = I.Cup + Sm.offCup;
+        for (int t = tid; t < Sm.nm * Sm.ldc; t += nt) CupM[t] = 0.f;
+        return;
     }
-    if (E.jp >= 0) {
-        float* Dp = I.D + Sp.offD;
-        float* CdnP_w = I.Cdn + Sp.offCdn;
-        const int* vrows_p = I.idx + Sp.offIdx + Sp.nm;
-        for (int t = threadIdx.x; t < Sp.nv * Sp.n; t += blockDim.x) {
-            int r = t / Sp.n, c = t % Sp.n;
-            float acc = 0.f;
-            for (int q = 0; q < nmj; ++q) acc += A3[r * nmj + q] * Cup_j[(size_t)q * Sj.ldc + c];
-            Dp[(size_t)c * np + vrows_p[r]] -= acc;
-        }
-        for (int t = threadIdx.x; t < Sp.nv * Sp.ldc; t += blockDim.x) {
-            int r = t / Sp.ldc, c = t % Sp.ldc;
-            float acc = 0.f;
-            if (c < Sm.n)
-                for (int q = 0; q < nvj; ++q) acc -= A4[r * nvj + q] * Cdn_j[(size_t)q * Sj.ldc + c];
-            CdnP_w[t] = acc;
-        }
+    float* Asm = esm;                   // M x N
+    float* stL = Asm + M * N;           // M x 32
+    float* stQ = stL + M * 32;          // 32 x N
+    float* Csm = stQ + 32 * N;          // N x ncol
+    __syncthreads();
+    rows_times_cols(Lrows, M, Sj.n, Dinv, np, cols, N, Asm, stL, stQ);
+    if (rank == 0) {
+        apply_coupling<true>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.D + Sm.offD, np, I.idx + Sm.offIdx, nullptr, 0, 0);
+    } else if (rank == 1) {
+        apply_coupling<false>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, nullptr, np, nullptr, I.Cup + Sm.offCup, Sm.ldc,
+                              Sm.ldc);
+    } else if (rank == 2) {
+        apply_coupling<true>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.D + Sp.offD, np, I.idx + Sp.offIdx + Sp.nm,
+                             nullptr, 0, 0);
+    } else {
+        apply_coupling<false>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, nullptr, np, nullptr, I.Cdn + Sp.offCdn, Sp.ldc,
+                              Sp.ldc);
     }
 }
 
@@ -268,9 +313,18 @@ __global__ void k_if_residual(IfPtrs I, const int* row_member, int nrows, int fi
     if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(I.rhs[row]));
 }
 
+// Warp-cooperative dot product of a row-major matrix row with a shared vector.
+__device__ __forceinline__ float warp_dot(const float* row, const float* v, int n) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+    for (int c = lane; c < n; c += 32) acc += row[c] * v[c];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 // forward: y_j = Dinv_j b_j (stored in place), then push into the neighbours
 __global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float y[];
+    extern __shared__ float fsm[];
     const int e = blockIdx.x;
     if (e >= nel) return;
     const ElimDev E = el[e];
@@ -278,10 +332,22 @@ __global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, in
     const int np = I.npad;
     const float* Dinv = I.Dinv + Sj.offD;
     float* bj = I.bq + Sj.col0;
+    float* bs = fsm;            // n_j
+    float* y = fsm + np;        // n_j
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bs[r] = bj[r];
+    __syncthreads();
     for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
-        float acc = 0.f;
-        for (int c = 0; c < Sj.n; ++c) acc += Dinv[(size_t)c * np + r] * bj[c];
-        y[r] = acc;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = 0;
+        for (; c + 3 < Sj.n; c += 4) {
+            a0 += Dinv[(size_t)c * np + r] * bs[c];
+            a1 += Dinv[(size_t)(c + 1) * np + r] * bs[c + 1];
+            a2 += Dinv[(size_t)(c + 2) * np + r] * bs[c + 2];
+            a3 += Dinv[(size_t)(c + 3) * np + r] * bs[c + 3];
+        }
+        for (; c < Sj.n; ++c) a0 += Dinv[(size_t)c * np + r] * bs[c];
+        y[r] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bj[r] = y[r];
@@ -290,10 +356,9 @@ __global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, in
         const float* Rup = I.Rup + Sj.offRup;
         const int* mrows_m = I.idx + Sm.offIdx;
         float* bm = I.bq + Sm.col0;
-        for (int r = threadIdx.x; r < Sm.nm; r += blockDim.x) {
-            float acc = 0.f;
-            for (int c = 0; c < Sj.n; ++c) acc += Rup[(size_t)r * Sj.n + c] * y[c];
-            bm[mrows_m[r]] -= acc;
+        for (int r = warp; r < Sm.nm; r += nwarp) {
+            const float acc = warp_dot(Rup + (size_t)r * Sj.n, y, Sj.n);
+            if ((threadIdx.x & 31) == 0) bm[mrows_m[r]] -= acc;
         }
     }
     if (E.jp >= 0) {
@@ -301,17 +366,16 @@ __global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, in
         const float* Rdn = I.Rdn + Sj.offRdn;
         const int* vrows_p = I.idx + Sp.offIdx + Sp.nm;
         float* bp = I.bq + Sp.col0;
-        for (int r = threadIdx.x; r < Sp.nv; r += blockDim.x) {
-            float acc = 0.f;
-            for (int c = 0; c < Sj.n; ++c) acc += Rdn[(size_t)r * Sj.n + c] * y[c];
-            bp[vrows_p[r]] -= acc;
+        for (int r = warp; r < Sp.nv; r += nwarp) {
+            const float acc = warp_dot(Rdn + (size_t)r * Sj.n, y, Sj.n);
+            if ((threadIdx.x & 31) == 0) bp[vrows_p[r]] -= acc;
         }
     }
 }
 
 // backward: x_j = y_j - Qv (Cdn_j x_jm) - Qm (Cup_j x_jp)
 __global__ void __launch_bounds__(256) k_bcr_bwd(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float t[];
+    extern __shared__ float bsm[];
     const int e = blockIdx.x;
     if (e >= nel) return;
     const ElimDev E = el[e];
@@ -320,26 +384,29 @@ __global__ void __launch_bounds__(256) k_bcr_bwd(IfPtrs I, const ElimDev* el, in
     const float* Dinv = I.Dinv + Sj.offD;
     const int* mrows_j = I.idx + Sj.offIdx;
     const int* vrows_j = mrows_j + Sj.nm;
-    float* tv = t;             // nv
-    float* tm = t + Sj.nv;     // nm
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    float* xm = bsm;              // n_jm
+    float* xp = bsm + np;         // n_jp
+    float* tv = bsm + 2 * np;     // nv_j
+    float* tm = tv + np;          // nm_j
     const SlabDev Sm = I.slabs[E.jm];
+    for (int c = threadIdx.x; c < Sm.n; c += blockDim.x) xm[c] = I.bq[Sm.col0 + c];
+    const int nmj = E.jp >= 0 ? Sj.nm : 0;
+    SlabDev Sp{};
+    if (E.jp >= 0) {
+        Sp = I.slabs[E.jp];
+        for (int c = threadIdx.x; c < Sp.n; c += blockDim.x) xp[c] = I.bq[Sp.col0 + c];
+    }
+    __syncthreads();
     const float* Cdn_j = I.Cdn + Sj.offCdn;
     const float* Cup_j = I.Cup + Sj.offCup;
-    const float* xm = I.bq + Sm.col0;
-    for (int q = threadIdx.x; q < Sj.nv; q += blockDim.x) {
-        float acc = 0.f;
-        for (int c = 0; c < Sm.n; ++c) acc += Cdn_j[(size_t)q * Sj.ldc + c] * xm[c];
-        tv[q] = acc;
+    for (int q = warp; q < Sj.nv; q += nwarp) {
+        const float acc = warp_dot(Cdn_j + (size_t)q * Sj.ldc, xm, Sm.n);
+        if ((threadIdx.x & 31) == 0) tv[q] = acc;
     }
-    const int nmj = E.jp >= 0 ? Sj.nm : 0;
-    if (E.jp >= 0) {
-        const SlabDev Sp = I.slabs[E.jp];
-        const float* xp = I.bq + Sp.col0;
-        for (int q = threadIdx.x; q < Sj.nm; q += blockDim.x) {
-            float acc = 0.f;
-            for (int c = 0; c < Sp.n; ++c) acc += Cup_j[(size_t)q * Sj.ldc + c] * xp[c];
-            tm[q] = acc;
-        }
+    for (int q = warp; q < nmj; q += nwarp) {
+        const float acc = warp_dot(Cup_j + (size_t)q * Sj.ldc, xp, Sp.n);
+        if ((threadIdx.x & 31) == 0) tm[q] = acc;
     }
     __syncthreads();
     float* xj = I.bq + Sj.col0;
@@ -374,13 +441,6 @@ cudaError_t bcr_fill(const IfPtrs& I, int nslab, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s) {
-    if (nel == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_bcr_elim<<<nel, 512, smem, s>>>(I, el, nel);
-    return cudaGetLastError();
-}
 
 cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int first, cudaStream_t s) {
     k_if_residual<<<(nrows + 255) / 256, 256, 0, s>>>(I, row_member, nrows, first);
@@ -389,13 +449,13 @@ cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int f
 
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_fwd<<<nel, 256, sizeof(float) * nmax, s>>>(I, el, nel);
+    k_bcr_fwd<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel);
     return cudaGetLastError();
 }
 
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_bwd<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel);
+    k_bcr_bwd<<<nel, 256, sizeof(float) * 4 * nmax, s>>>(I, el, nel);
     return cudaGetLastError();
 }
 
@@ -404,38 +464,36 @@ cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-#include <cooperative_groups.h>
-namespace cg = cooperative_groups;
-
-constexpr int GJ_NB = 32;   // panel width
-constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
-constexpr int GJ_THREADS = 512;
-
 // ---------------------------------------------------------------------------
 // Slab inverse through a blocked LU factorisation with partial pivoting
 // (FP32, column-major np x np, in place in D, inverse written to Dinv).
 // Phase 1 (cluster-synchronised per panel of GJ_NB columns): every CTA of
-// the cluster factors the panel redundantly in shared memory, the owner
-// writes it back, and each CTA applies the interchanges to the columns it
-// owns, forms their U12 rows and updates their trailing part.
+// the cluster factors the panel redundantly in shared memory and inverts its
+// unit-lower and upper diagonal blocks; the owner writes the panel and the
+// two block inverses back, and each CTA applies the interchanges to the
+// columns it owns, forms their U12 rows (L11^-1 A12) and updates their
+// trailing part (A22 -= L21 U12).
 // Phase 2 (independent per CTA): the columns of the inverse owned by a CTA
-// are solved from P A = L U: column j = U^-1 L^-1 e_{q(j)}.
+// are solved from P A = L U (column j = U^-1 L^-1 e_{q(j)}) panel by panel,
+// each diagonal block applied through its kept inverse.
 // ---------------------------------------------------------------------------
+
 __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int e = blockIdx.x / GJ_CL;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
     const int np = I.npad;
     const int npan = (np + GJ_NB - 1) / GJ_NB;
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     extern __shared__ __align__(16) float lsm[];
     float* Ps = lsm;                           // [c][r], GJ_NB * np
-    float* Xs = Ps + GJ_NB * np;               // [jj][r], GJ_NB * np
-    float* Upy = Xs + GJ_NB * np;              // [c][jj], GJ_NB * ncmax
-    int* piv = (int*)(Upy + GJ_NB * ncmax);    // np
+    float* Xs = Ps + GJ_NB * np;               // [jj][r], GJ_NB * max(np, ncmax)
+    float* Upy = Xs + GJ_NB * max(np, ncmax);  // [c][jj], max(GJ_NB * ncmax, np)
+    int* piv = (int*)(Upy + max(GJ_NB * ncmax, np));  // np
     int* ownc = piv + np;                      // ncmax
-    int* qpos = ownc + ncmax;                  // np: position of the unit entry of P e_j
+    int* qpos = ownc + ncmax;                  // np
     __shared__ float redv[32];
     __shared__ int redi[32];
     __shared__ int nown;
@@ -460,10 +518,8 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         cluster.sync();
         const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
         if (active)
-            for (int t = tid; t < b * (np - k0); t += nt) {
-                int c = t / (np - k0), r = k0 + t % (np - k0);
-                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
-            }
+            for (int c = warp; c < b; c += nwarp)
+                for (int r = k0 + lane; r < np; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
         cluster.sync();
         if (!active) continue;
         for (int c = 0; c < b; ++c) {
@@ -471,67 +527,67 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             float best = -1.f;
             int bi = r0;
             for (int r = r0 + tid; r < np; r += nt) {
-                float v = fabsf(Ps[c * np + r]);
+                const float v = fabsf(Ps[c * np + r]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int o = 16; o; o >>= 1) {
-                float ov = __shfl_xor_sync(0xffffffffu, best, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
-            if ((tid & 31) == 0) { redv[tid >> 5] = best; redi[tid >> 5] = bi; }
+            if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
             __syncthreads();
             if (tid < 32) {
-                float v = tid < (nt >> 5) ? redv[tid] : -1.f;
-                int ii = tid < (nt >> 5) ? redi[tid] : 0x7fffffff;
+                float v = tid < nwarp ? redv[tid] : -1.f;
+                int ii = tid < nwarp ? redi[tid] : 0x7fffffff;
                 for (int o = 16; o; o >>= 1) {
-                    float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                    int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+                    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
                     if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
                 }
                 if (tid == 0) piv[r0] = ii;
             }
             __syncthreads();
             const int p = piv[r0];
-            if (p != r0)
-                for (int cc = tid; cc < b; cc += nt) {
-                    float t0 = Ps[cc * np + r0];
-                    Ps[cc * np + r0] = Ps[cc * np + p];
-                    Ps[cc * np + p] = t0;
-                }
+            if (p != r0 && tid < b) {
+                const float t0 = Ps[tid * np + r0];
+                Ps[tid * np + r0] = Ps[tid * np + p];
+                Ps[tid * np + p] = t0;
+            }
             __syncthreads();
             float a = Ps[c * np + r0];
             if (a == 0.f) { singular = true; a = 1e-30f; }
-            const float ia = (float)(1.0 / (double)a);
+            const float ia = 1.f / a;
             for (int r = r0 + 1 + tid; r < np; r += nt) Ps[c * np + r] *= ia;
             __syncthreads();
-            for (int t = tid; t < (b - c - 1) * (np - r0 - 1); t += nt) {
-                int cc = c + 1 + t / (np - r0 - 1), r = r0 + 1 + t % (np - r0 - 1);
-                Ps[cc * np + r] -= Ps[c * np + r] * Ps[cc * np + r0];
+            for (int cc = c + 1 + warp; cc < b; cc += nwarp) {
+                const float u = Ps[cc * np + r0];
+                for (int r = r0 + 1 + lane; r < np; r += 32) Ps[cc * np + r] -= Ps[c * np + r] * u;
             }
             __syncthreads();
         }
-        if (q % GJ_CL == rank)
-            for (int t = tid; t < b * (np - k0); t += nt) {
-                int c = t / (np - k0), r = k0 + t % (np - k0);
-                A[(size_t)(k0 + c) * np + r] = Ps[c * np + r];
-            }
+        // interchanges on owned columns
         const int no = nown;
-        // interchanges on every owned column outside the panel
         for (int jj = tid; jj < no; jj += nt) {
             const int j = ownc[jj];
             if (j >= k0 && j < k0 + b) continue;
             float* col = A + (size_t)j * np;
             for (int c = 0; c < b; ++c) {
-                int p = piv[k0 + c];
-                if (p != k0 + c) { float t0 = col[k0 + c]; col[k0 + c] = col[p]; col[p] = t0; }
+                const int p = piv[k0 + c];
+                if (p != k0 + c) { const float t0 = col[k0 + c]; col[k0 + c] = col[p]; col[p] = t0; }
             }
         }
         __syncthreads();
-        // U12 = L11^-1 A12 for owned trailing columns (one thread per column)
+        if (q % GJ_CL == rank)
+            for (int c = warp; c < b; c += nwarp)
+                for (int r = k0 + lane; r < np; r += 32) A[(size_t)(k0 + c) * np + r] = Ps[c * np + r];
+        // U12 = L11^-1 A12 on owned trailing columns, by substitution (one thread per column)
         for (int jj = tid; jj < no; jj += nt) {
             const int j = ownc[jj];
-            if (j < k0 + b) continue;
+            if (j < k0 + b) {
+                for (int c = 0; c < GJ_NB; ++c) Upy[c * ncmax + jj] = 0.f;
+                continue;
+            }
             float* col = A + (size_t)j * np;
             float x[GJ_NB];
 #pragma unroll
@@ -554,13 +610,14 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         if (r1 < np) {
             const int ntr = (np - r1) / 4, ntc = (no + 3) / 4;
             for (int t = tid; t < ntr * ntc; t += nt) {
-                const int r = r1 + (t % ntr) * 4, jj0 = (t / ntr) * 4;
+                const int tc = t / ntr;
+                const int r = r1 + (t - tc * ntr) * 4, jj0 = tc * 4;
                 float acc[4][4];
                 int jcol[4];
                 bool skip[4];
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
-                    int jj = jj0 + y;
+                    const int jj = jj0 + y;
                     jcol[y] = jj < no ? ownc[jj] : -1;
                     skip[y] = jcol[y] < r1;
 #pragma unroll
@@ -571,7 +628,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                     const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
                     float av[4];
 #pragma unroll
-                    for (int y = 0; y < 4; ++y) av[y] = skip[y] ? 0.f : Upy[c * ncmax + jj0 + y];
+                    for (int y = 0; y < 4; ++y) av[y] = (jj0 + y < no) ? Upy[c * ncmax + jj0 + y] : 0.f;
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -591,11 +648,10 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     if (!active) return;
     // ---------------- phase 2: owned columns of the inverse ----------------
     if (tid == 0) {
-        // rowperm[i] = original row at position i; qpos[j] = position of original row j
-        int* rowperm = (int*)Upy;
+        int* rowperm = (int*)Upy;  // rowperm[i] = original row at position i
         for (int i = 0; i < np; ++i) rowperm[i] = i;
         for (int c = 0; c < np; ++c) {
-            int p = piv[c], t0 = rowperm[c];
+            const int p = piv[c], t0 = rowperm[c];
             rowperm[c] = rowperm[p];
             rowperm[p] = t0;
         }
@@ -605,87 +661,95 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     const int no = nown;
     for (int j0 = 0; j0 < no; j0 += GJ_NB) {
         const int nb = min(GJ_NB, no - j0);
-        for (int t = tid; t < GJ_NB * np; t += nt) {
-            int jj = t / np, r = t % np;
-            Xs[t] = (jj < nb && r == qpos[ownc[j0 + jj]]) ? 1.f : 0.f;
-        }
+        for (int jj = warp; jj < GJ_NB; jj += nwarp)
+            for (int r = lane; r < np; r += 32) Xs[jj * np + r] = (jj < nb && r == qpos[ownc[j0 + jj]]) ? 1.f : 0.f;
         __syncthreads();
-        // forward with unit L, panel by panel
+        // forward with unit L
         for (int q = 0; q < npan; ++q) {
             const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
-            for (int t = tid; t < b * (np - k0); t += nt) {
-                int c = t / (np - k0), r = k0 + t % (np - k0);
-                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
-            }
+            for (int c = warp; c < b; c += nwarp)
+                for (int r = k0 + lane; r < np; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
             __syncthreads();
             for (int jj = tid; jj < nb; jj += nt) {
                 float* xc = Xs + jj * np;
-                for (int c = 0; c < b; ++c) {
-                    const float xv = xc[k0 + c];
-                    for (int c2 = c + 1; c2 < b; ++c2) xc[k0 + c2] -= Ps[c * np + k0 + c2] * xv;
-                }
+                float x[GJ_NB];
+#pragma unroll
+                for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? xc[k0 + c] : 0.f;
+#pragma unroll
+                for (int c = 0; c < GJ_NB; ++c)
+#pragma unroll
+                    for (int c2 = c + 1; c2 < GJ_NB; ++c2)
+                        if (c2 < b) x[c2] -= Ps[c * np + k0 + c2] * x[c];
+#pragma unroll
+                for (int c = 0; c < GJ_NB; ++c)
+                    if (c < b) xc[k0 + c] = x[c];
             }
             __syncthreads();
             const int r1 = k0 + b;
-            for (int t = tid; t < (np - r1) * nb; t += nt) {
-                int jj = t / (np - r1), r = r1 + t % (np - r1);
-                float* xc = Xs + jj * np;
-                float acc = xc[r];
-                for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * xc[k0 + c];
-                xc[r] = acc;
-            }
+            for (int jj = warp; jj < nb; jj += nwarp)
+                for (int r = r1 + lane; r < np; r += 32) {
+                    float acc = Xs[jj * np + r];
+                    for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * Xs[jj * np + k0 + c];
+                    Xs[jj * np + r] = acc;
+                }
             __syncthreads();
         }
-        // backward with U, panel by panel from the last
+        // backward with U
         for (int q = npan - 1; q >= 0; --q) {
             const int k0 = q * GJ_NB, b = min(GJ_NB, np - k0);
-            for (int t = tid; t < b * (k0 + b); t += nt) {
-                int c = t / (k0 + b), r = t % (k0 + b);
-                Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
-            }
+            for (int c = warp; c < b; c += nwarp)
+                for (int r = lane; r < k0; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
+            for (int c = warp; c < b; c += nwarp)
+                for (int r = k0 + lane; r < k0 + b; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
             __syncthreads();
             for (int jj = tid; jj < nb; jj += nt) {
                 float* xc = Xs + jj * np;
-                for (int c = b - 1; c >= 0; --c) {
-                    const float xv = xc[k0 + c] / Ps[c * np + k0 + c];
-                    xc[k0 + c] = xv;
-                    for (int c2 = 0; c2 < c; ++c2) xc[k0 + c2] -= Ps[c * np + k0 + c2] * xv;
+                float x[GJ_NB];
+#pragma unroll
+                for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? xc[k0 + c] : 0.f;
+#pragma unroll
+                for (int c = GJ_NB - 1; c >= 0; --c)
+                    if (c < b) {
+                        x[c] = x[c] / Ps[c * np + k0 + c];
+#pragma unroll
+                        for (int c2 = 0; c2 < GJ_NB; ++c2)
+                            if (c2 < c) x[c2] -= Ps[c * np + k0 + c2] * x[c];
+                    }
+#pragma unroll
+                for (int c = 0; c < GJ_NB; ++c)
+                    if (c < b) xc[k0 + c] = x[c];
+            }
+            __syncthreads();
+            for (int jj = warp; jj < nb; jj += nwarp)
+                for (int r = lane; r < k0; r += 32) {
+                    float acc = Xs[jj * np + r];
+                    for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * Xs[jj * np + k0 + c];
+                    Xs[jj * np + r] = acc;
                 }
-            }
-            __syncthreads();
-            for (int t = tid; t < k0 * nb; t += nt) {
-                int jj = t / k0, r = t % k0;
-                float* xc = Xs + jj * np;
-                float acc = xc[r];
-                for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * xc[k0 + c];
-                xc[r] = acc;
-            }
             __syncthreads();
         }
-        for (int t = tid; t < nb * np; t += nt) {
-            int jj = t / np, r = t % np;
-            Ainv[(size_t)ownc[j0 + jj] * np + r] = Xs[jj * np + r];
-        }
+        for (int jj = warp; jj < nb; jj += nwarp)
+            for (int r = lane; r < np; r += 32) Ainv[(size_t)ownc[j0 + jj] * np + r] = Xs[jj * np + r];
         __syncthreads();
     }
     if (singular && tid == 0) atomicOr(status, ST_SINGULAR);
 }
 
 size_t lu_smem(int np) {
-    int npan = (np + GJ_NB - 1) / GJ_NB;
-    int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
-    size_t ncm = std::max((size_t)GJ_NB * ncmax, (size_t)np);
-    return sizeof(float) * (2 * (size_t)GJ_NB * np + ncm) + sizeof(int) * ((size_t)np + ncmax + np) + 16;
+    const int npan = (np + GJ_NB - 1) / GJ_NB;
+    const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
+    const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
+    const size_t xs = (size_t)GJ_NB * std::max(np, ncmax);
+    return sizeof(float) * ((size_t)GJ_NB * np + xs + up) +
+           sizeof(int) * ((size_t)np + ncmax + np) + 16;
 }
 
-cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
-    if (nel == 0) return cudaSuccess;
-    size_t smem = lu_smem(I.npad);
-    cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+
+static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
+                                  void** args) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nel * GJ_CL);
-    cfg.blockDim = dim3(GJ_THREADS);
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -695,5 +759,29 @@ cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_lu_inverse, I, el, nel, status);
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
+cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
+    if (nel == 0) return cudaSuccess;
+    const size_t smem = lu_smem(I.npad);
+    cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel, &status};
+    return launch_cluster((const void*)k_lu_inverse, nel * GJ_CL, GJ_THREADS, smem, s, args);
+}
+
+size_t elim_smem_bytes(int nmv, int nmax) {
+    // Asm (nmv^2) + stL (nmv*32) + stQ (32*nmv) + Csm (nmv * nmax)
+    return sizeof(float) * ((size_t)nmv * nmv + 64 * (size_t)nmv + (size_t)nmv * nmax) + 16;
+}
+
+cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s) {
+    if (nel == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel};
+    return launch_cluster((const void*)k_bcr_elim, nel * GJ_CL, EL_THREADS, smem, s, args);
 }

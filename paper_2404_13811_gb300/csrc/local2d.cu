@@ -15,6 +15,11 @@
 // pivot reciprocal are formed in FP64, the sweeps run in FP32, and each
 // right-hand side is refined with FP64 residuals of the unscaled operator
 // until |r|_inf <= ir_tol |b|_inf.
+//
+// FP64 division and square root are avoided in the hot loops (GB300 has a
+// narrow FP64 pipe): face transmissibilities come precomputed per problem,
+// reciprocals are an FP32 seed refined by two FP64 Newton steps, and the
+// Jacobi scale is an FP32 rsqrt used consistently on both sides.
 #include "mrcm_internal.cuh"
 #include <type_traits>
 
@@ -22,12 +27,13 @@ namespace {
 
 constexpr int NWARP = 8;
 
-__device__ __forceinline__ double psi_val(int m, int pos, int len) {
-    // P0: 1; P1: affine coordinate of the face centre, t in [-1, 1]
-    return m == 0 ? 1.0 : (2.0 * (pos + 0.5) / len - 1.0);
+// 1/x in FP64: FP32 reciprocal refined by two Newton steps (error ~ u_64).
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
 }
-
-__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
 
 // Box description shared by all threads of a CTA.
 struct Box {
@@ -36,6 +42,7 @@ struct Box {
     int kind[4];      // 0 Neumann, 1 Dirichlet, 2 Robin
     double val[4];    // physical data (g or z)
     double alpha;
+    double rlen[4];   // 1 / (faces on the side)
 };
 
 // side offsets into the per-side boundary arrays: x sides have ny faces,
@@ -44,66 +51,56 @@ __device__ __forceinline__ int side_off(const Box& B, int sid) {
     return sid == 0 ? 0 : sid == 1 ? B.ny : sid == 2 ? 2 * B.ny : 2 * B.ny + B.nx;
 }
 
-// Shared-memory layout of the box operator.
+// P0: 1; P1: affine coordinate of the face centre along the side, in [-1, 1].
+__device__ __forceinline__ double psi_val(int m, int pos, int len, double rlen) {
+    return m == 0 ? 1.0 : (double)(2 * pos + 1 - len) * rlen;
+}
+
+// Shared-memory copy of the box operator.
 struct Ops {
-    double* Kh;   // (nx + 2) * (ny + 2) permeability with a halo ring (0 outside the domain)
     double* cd;   // diagonal
     double* cx;   // coupling of cell (i, j) with (i + 1, j)
     double* cy;   // coupling of cell (i, j) with (i, j + 1)
+    double* hk;   // h / (2K) per cell, x and y interleaved [2n]
     double* bT;   // boundary-face transmissibility per side
     double* bB;   // Robin beta per side
     double* dsc;  // Jacobi scale (1 in the FP64 form)
 };
 
-// Loads K, builds all face transmissibilities of the box operator.
-__device__ void build_ops(const Box& B, const MemberDev& md, const double* __restrict__ K,
-                          Ops& O) {
-    const int nxh = B.nx + 2;
-    const double* Km = K + md.cell_off;
-    for (int t = threadIdx.x; t < (B.nx + 2) * (B.ny + 2); t += blockDim.x) {
-        int ih = t % nxh, jh = t / nxh;
-        int gx = B.lo[0] + ih - 1, gy = B.lo[1] + jh - 1;
-        double k = 0.0;
-        if (gx >= 0 && gx < md.n[0] && gy >= 0 && gy < md.n[1]) k = Km[gx + (long long)md.n[0] * gy];
-        O.Kh[t] = k;
-    }
-    __syncthreads();
-    const double hx = md.h[0], hy = md.h[1];
-    const double ax = hy, ay = hx;  // face areas (normal to x, normal to y)
+// Loads the face coefficients of the box and forms the boundary faces.
+__device__ void build_ops(const Box& B, const MemberDev& md, const DevPtrs& P, Ops& O) {
+    const double* Tf = P.Tf + md.cell_off * 3;
+    const double* hkg = P.hk + md.cell_off * 3;
+    const double* wh = P.wh + md.cell_off * 3;
+    const int nxg = md.n[0];
     for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
-        int i = c % B.nx, j = c / B.nx;
-        double kc = O.Kh[(j + 1) * nxh + i + 1];
-        double txp = 0.0, typ = 0.0;
-        if (i < B.nx - 1) {
-            double kr = O.Kh[(j + 1) * nxh + i + 2];
-            txp = ax * 2.0 * kc * kr / (hx * (kc + kr));
-        }
-        if (j < B.ny - 1) {
-            double ku = O.Kh[(j + 2) * nxh + i + 1];
-            typ = ay * 2.0 * kc * ku / (hy * (kc + ku));
-        }
-        O.cx[c] = txp;
-        O.cy[c] = typ;
+        const int i = c % B.nx, j = c / B.nx;
+        const long long g = (B.lo[0] + i) + (long long)nxg * (B.lo[1] + j);
+        O.cx[c] = i < B.nx - 1 ? Tf[g * 3 + 0] : 0.0;
+        O.cy[c] = j < B.ny - 1 ? Tf[g * 3 + 1] : 0.0;
+        O.hk[2 * c] = hkg[g * 3 + 0];
+        O.hk[2 * c + 1] = hkg[g * 3 + 1];
     }
-    // boundary faces
+    const double ax = md.h[1], ay = md.h[0];  // face areas (normal to x, normal to y)
     for (int sid = 0; sid < 4; ++sid) {
         const int a = sid >> 1;
         const int len = a == 0 ? B.ny : B.nx;
         const double area = a == 0 ? ax : ay;
-        const double h = a == 0 ? hx : hy;
         const int off = side_off(B, sid);
         for (int pos = threadIdx.x; pos < len; pos += blockDim.x) {
-            int i, j, io, jo;
-            if (a == 0) { j = pos; i = (sid == 0) ? 0 : B.nx - 1; io = (sid == 0) ? i - 1 : i + 1; jo = j; }
-            else        { i = pos; j = (sid == 2) ? 0 : B.ny - 1; jo = (sid == 2) ? j - 1 : j + 1; io = i; }
-            double kin = O.Kh[(j + 1) * nxh + i + 1];
+            int i, j;
+            if (a == 0) { j = pos; i = (sid == 0) ? 0 : B.nx - 1; }
+            else        { i = pos; j = (sid == 2) ? 0 : B.ny - 1; }
+            const long long g = (B.lo[0] + i) + (long long)nxg * (B.lo[1] + j);
+            const double hin = hkg[g * 3 + a];
             double T = 0.0, beta = 0.0;
             if (B.kind[sid] == 2) {
-                double kout = O.Kh[(jo + 1) * nxh + io + 1];
-                beta = B.alpha * md.Hw[a] / harm(kin, kout);
-                T = area / (h / (2.0 * kin) + beta);
+                // the face to the outside cell: owned by the lower of the two cells
+                const long long gf = (sid & 1) ? g : g - (a == 0 ? 1 : nxg);
+                beta = B.alpha * wh[gf * 3 + a];
+                T = area * rcp64(hin + beta);
             } else if (B.kind[sid] == 1) {
-                T = 2.0 * area * kin / h;
+                T = area * rcp64(hin);
             }
             O.bT[off + pos] = T;
             O.bB[off + pos] = beta;
@@ -111,7 +108,7 @@ __device__ void build_ops(const Box& B, const MemberDev& md, const double* __res
     }
     __syncthreads();
     for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
-        int i = c % B.nx, j = c / B.nx;
+        const int i = c % B.nx, j = c / B.nx;
         double d = O.cx[c] + O.cy[c];
         if (i > 0) d += O.cx[c - 1];
         if (j > 0) d += O.cy[c - B.nx];
@@ -125,8 +122,8 @@ __device__ void build_ops(const Box& B, const MemberDev& md, const double* __res
 }
 
 // (A x)_c for the unscaled FP64 operator.
-__device__ __forceinline__ double apply_A(const Box& B, const Ops& O, const double* x, int c) {
-    int i = c % B.nx, j = c / B.nx;
+__device__ __forceinline__ double apply_A(const Box& B, const Ops& O, const double* x, int i, int j) {
+    const int c = j * B.nx + i;
     double s = O.cd[c] * x[c];
     if (i > 0) s -= O.cx[c - 1] * x[c - 1];
     if (i < B.nx - 1) s -= O.cx[c] * x[c + 1];
@@ -156,8 +153,7 @@ __device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
                 if (lane == 0) *bad = 1;
                 piv = 1.0;
             }
-            const double ipd = 1.0 / piv;
-            const T ip = (T)ipd;
+            const T ip = (T)rcp64(piv);
             if (lane == k) {
 #pragma unroll
                 for (int c = 0; c < BW; ++c) a[c] = (c == k) ? ip : a[c] * ip;
@@ -180,21 +176,19 @@ __device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
 // Block LDL^T factorisation: Sinv[j] = S_j^{-1}.  cys = scaled line coupling
 // (type T).  All threads participate.
 template <typename T, int BW>
-__device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* Sbuf, T* rowbuf,
-                           int* bad) {
+__device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* Sbuf, T* rowbuf, int* bad) {
     const int b = B.nx, nb = B.ny;
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
         cys[c] = (T)(O.cy[c] * O.dsc[c] * ((c + b < B.n) ? O.dsc[c + b] : 0.0));
-    }
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
         for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-            int i = t / b, k = t % b;
-            int ci = j * b + i, ck = j * b + k;
+            const int i = t / b, k = t - (t / b) * b;
+            const int ci = j * b + i, ck = j * b + k;
             if (i == k) {
                 double s = O.cd[ci] * O.dsc[ci] * O.dsc[ci];
                 if (j > 0) {
-                    double cc = (double)cys[ci - b];
+                    const double cc = (double)cys[ci - b];
                     s -= cc * cc * (double)Sinv[((j - 1) * b + i) * b + i];
                 }
                 Sbuf[t] = (T)s;
@@ -212,25 +206,29 @@ __device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* Sbuf,
     }
 }
 
-// One warp solves (scaled) S-sweeps in place: on entry w holds the scaled
-// right-hand side, on exit the scaled solution.
+// One warp sweeps in place: on entry w holds the scaled right-hand side, on
+// exit the scaled solution.
 template <typename T>
 __device__ void warp_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys, T* w, T* zbuf,
                             int b, int nb) {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < nb; ++j) {
-        T z = T(0);
         if (lane < b) {
-            z = w[j * b + lane];
+            T z = w[j * b + lane];
             if (j > 0) z += cys[(j - 1) * b + lane] * w[(j - 1) * b + lane];
             zbuf[lane] = z;
         }
         __syncwarp();
         if (lane < b) {
             const T* S = Sinv + (size_t)j * b * b;
-            T acc = T(0);
-            for (int k = 0; k < b; ++k) acc += S[k * b + lane] * zbuf[k];
-            w[j * b + lane] = acc;
+            T acc0 = T(0), acc1 = T(0);
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                acc0 += S[k * b + lane] * zbuf[k];
+                acc1 += S[(k + 1) * b + lane] * zbuf[k + 1];
+            }
+            if (k < b) acc0 += S[k * b + lane] * zbuf[k];
+            w[j * b + lane] = acc0 + acc1;
         }
         __syncwarp();
     }
@@ -239,9 +237,14 @@ __device__ void warp_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cy
         __syncwarp();
         if (lane < b) {
             const T* S = Sinv + (size_t)j * b * b;
-            T acc = T(0);
-            for (int k = 0; k < b; ++k) acc += S[k * b + lane] * zbuf[k];
-            w[j * b + lane] += acc;
+            T acc0 = T(0), acc1 = T(0);
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                acc0 += S[k * b + lane] * zbuf[k];
+                acc1 += S[(k + 1) * b + lane] * zbuf[k + 1];
+            }
+            if (k < b) acc0 += S[k * b + lane] * zbuf[k];
+            w[j * b + lane] += acc0 + acc1;
         }
         __syncwarp();
     }
@@ -249,80 +252,83 @@ __device__ void warp_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cy
 
 // Right-hand side generators -------------------------------------------------
 
-// Basis problem k: Robin data psi_m on side sk of the box (homogeneous elsewhere).
+// Basis problem: Robin data psi_m on side sk of the box, homogeneous elsewhere.
 struct RhsBasis {
     int sk, m;
-    __device__ double operator()(const Box& B, const Ops& O, int c) const {
-        int i = c % B.nx, j = c / B.nx;
-        int a = sk >> 1;
-        bool on = (sk == 0 && i == 0) || (sk == 1 && i == B.nx - 1) || (sk == 2 && j == 0) ||
-                  (sk == 3 && j == B.ny - 1);
+    __device__ double operator()(const Box& B, const Ops& O, int i, int j) const {
+        const int a = sk >> 1;
+        const bool on = (sk == 0 && i == 0) || (sk == 1 && i == B.nx - 1) || (sk == 2 && j == 0) ||
+                        (sk == 3 && j == B.ny - 1);
         if (!on) return 0.0;
-        int pos = a == 0 ? j : i;
-        int len = a == 0 ? B.ny : B.nx;
-        return O.bT[side_off(B, sk) + pos] * psi_val(m, pos, len);
+        const int pos = a == 0 ? j : i;
+        const int len = a == 0 ? B.ny : B.nx;
+        return O.bT[side_off(B, sk) + pos] * psi_val(m, pos, len, B.rlen[sk]);
     }
 };
 
-// Sources f, g, z plus Robin data lam (may be null = 0).
-struct RhsSource {
-    const double* f;   // member cell array
-    int nxg;           // member grid nx
-    double vol, ax, ay;
-    const double* lam; // per-side Robin data (side_off layout) or null
-    __device__ double operator()(const Box& B, const Ops& O, int c) const {
-        int i = c % B.nx, j = c / B.nx;
-        double r = f[(B.lo[0] + i) + (long long)nxg * (B.lo[1] + j)] * vol;
-        int sides[4] = {i == 0 ? 0 : -1, i == B.nx - 1 ? 1 : -1, j == 0 ? 2 : -1, j == B.ny - 1 ? 3 : -1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int sid = sides[q];
-            if (sid < 0) continue;
-            int pos = (sid >> 1) == 0 ? j : i;
-            double area = (sid >> 1) == 0 ? ax : ay;
-            if (B.kind[sid] == 1) r += O.bT[side_off(B, sid) + pos] * B.val[sid];
-            else if (B.kind[sid] == 0) r -= area * B.val[sid];
-            else if (lam) r += O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos];
-        }
-        return r;
-    }
+// Fixed right-hand side kept in shared memory (sources + boundary data).
+struct RhsStored {
+    const double* b;
+    __device__ double operator()(const Box& B, const Ops&, int i, int j) const { return b[j * B.nx + i]; }
 };
+
+// f |c| + Dirichlet / Neumann data + Robin data lam (lam may be null).
+__device__ double source_rhs(const Box& B, const Ops& O, const double* fm, int nxg, double vol, double ax,
+                             double ay, const double* lam, int i, int j) {
+    double r = fm[(B.lo[0] + i) + (long long)nxg * (B.lo[1] + j)] * vol;
+    const int sides[4] = {i == 0 ? 0 : -1, i == B.nx - 1 ? 1 : -1, j == 0 ? 2 : -1, j == B.ny - 1 ? 3 : -1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int sid = sides[q];
+        if (sid < 0) continue;
+        const int pos = (sid >> 1) == 0 ? j : i;
+        const double area = (sid >> 1) == 0 ? ax : ay;
+        if (B.kind[sid] == 1) r += O.bT[side_off(B, sid) + pos] * B.val[sid];
+        else if (B.kind[sid] == 0) r -= area * B.val[sid];
+        else if (lam) r += O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos];
+    }
+    return r;
+}
 
 // Solves A x = b for one right-hand side with one warp.  FP64 form: one
 // solve.  Mixed form: FP32 sweeps + FP64 residual refinement.  Returns the
-// number of refinement steps.
+// number of sweeps (solves) performed.
 template <typename T, typename Rhs>
-__device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys, double* x,
-                          T* w, T* zbuf, const Rhs& rhs, double tol, int max_ir, int* noconv) {
+__device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys, double* x, T* w,
+                          T* zbuf, const Rhs& rhs, double tol, int max_ir, int* noconv) {
     const int lane = threadIdx.x & 31;
-    const int b = B.nx, nb = B.ny, n = B.n;
+    const int b = B.nx, nb = B.ny;
     if (std::is_same<T, double>::value) {
-        // FP64: w aliases x
-        for (int c = lane; c < n; c += 32) w[c] = (T)rhs(B, O, c);
+        for (int j = 0; j < nb; ++j)
+            for (int i = lane; i < b; i += 32) w[j * b + i] = (T)rhs(B, O, i, j);
         __syncwarp();
         warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
         return 1;
     } else {
         double bn = 0.0;
-        for (int c = lane; c < n; c += 32) {
-            double bc = rhs(B, O, c);
-            x[c] = 0.0;
-            w[c] = (T)(O.dsc[c] * bc);
-            bn = fmax(bn, fabs(bc));
-        }
+        for (int j = 0; j < nb; ++j)
+            for (int i = lane; i < b; i += 32) {
+                const int c = j * b + i;
+                const double bc = rhs(B, O, i, j);
+                x[c] = 0.0;
+                w[c] = (T)(O.dsc[c] * bc);
+                bn = fmax(bn, fabs(bc));
+            }
         for (int o = 16; o; o >>= 1) bn = fmax(bn, __shfl_xor_sync(0xffffffffu, bn, o));
         __syncwarp();
         int it = 0;
         for (; it < max_ir; ++it) {
             warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
-            for (int c = lane; c < n; c += 32) x[c] += O.dsc[c] * (double)w[c];
+            for (int c = lane; c < B.n; c += 32) x[c] += O.dsc[c] * (double)w[c];
             __syncwarp();
             double rn = 0.0;
-            for (int c = lane; c < n; c += 32) {
-                double r = rhs(B, O, c) - apply_A(B, O, x, c);
-                rn = fmax(rn, fabs(r));
-                w[c] = (T)(O.dsc[c] * r);
-            }
+            for (int j = 0; j < nb; ++j)
+                for (int i = lane; i < b; i += 32) {
+                    const int c = j * b + i;
+                    const double r = rhs(B, O, i, j) - apply_A(B, O, x, i, j);
+                    rn = fmax(rn, fabs(r));
+                    w[c] = (T)(O.dsc[c] * r);
+                }
             for (int o = 16; o; o >>= 1) rn = fmax(rn, __shfl_xor_sync(0xffffffffu, rn, o));
             __syncwarp();
             if (rn <= tol * bn || bn == 0.0) { ++it; break; }
@@ -332,8 +338,9 @@ __device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cy
     }
 }
 
-// Shared-memory carve-up -----------------------------------------------------
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// Shared-memory carve-up ----------------------------------------------------
 template <typename T>
 struct Carve {
     Ops O;
@@ -342,42 +349,35 @@ struct Carve {
     T* Sbuf;
     T* rowbuf;
     T* zbuf;   // NWARP * 32
+    double* bsrc; // n: fixed right-hand side of the particular problem
     double* X; // nrhs * n
     T* W;      // nrhs * n
     int* flags;
 };
 
-__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
-
 template <typename T>
 __host__ __device__ inline size_t carve_bytes(int nx, int ny, int nrhs) {
-    size_t n = (size_t)nx * ny;
-    size_t s = 0;
-    s += align16(sizeof(double) * (nx + 2) * (ny + 2));
-    s += align16(sizeof(double) * n) * 4;               // cd, cx, cy, dsc
-    s += align16(sizeof(double) * 2 * (nx + ny)) * 2;   // bT, bB
-    s += align16(sizeof(T) * n * nx);                    // Sinv (ny blocks of nx*nx)
-    s += align16(sizeof(T) * n);                         // cys
-    s += align16(sizeof(T) * nx * nx);                   // Sbuf
-    s += align16(sizeof(T) * 32);                        // rowbuf
-    s += align16(sizeof(T) * 32 * NWARP);                // zbuf
-    if (std::is_same<T, float>::value) s += align16(sizeof(double) * n * nrhs);  // X
-    s += align16(sizeof(T) * n * nrhs);                  // W
-    s += 64;                                             // flags
-    return s;
+    const size_t n = (size_t)nx * ny;
+    size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);  // cd cx cy dsc hk
+    s += align16(sizeof(double) * 2 * (nx + ny)) * 2;                                 // bT bB
+    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) + align16(sizeof(T) * nx * nx);
+    s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * NWARP) + align16(sizeof(double) * n);
+    if (std::is_same<T, float>::value) s += align16(sizeof(double) * n * nrhs);
+    s += align16(sizeof(T) * n * nrhs);
+    return s + 64;
 }
 
 template <typename T>
 __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
     Carve<T> C;
-    size_t n = (size_t)nx * ny;
+    const size_t n = (size_t)nx * ny;
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
-    C.O.Kh = (double*)take(sizeof(double) * (nx + 2) * (ny + 2));
     C.O.cd = (double*)take(sizeof(double) * n);
     C.O.cx = (double*)take(sizeof(double) * n);
     C.O.cy = (double*)take(sizeof(double) * n);
     C.O.dsc = (double*)take(sizeof(double) * n);
+    C.O.hk = (double*)take(sizeof(double) * 2 * n);
     C.O.bT = (double*)take(sizeof(double) * 2 * (nx + ny));
     C.O.bB = (double*)take(sizeof(double) * 2 * (nx + ny));
     C.Sinv = (T*)take(sizeof(T) * n * nx);
@@ -385,6 +385,7 @@ __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
     C.Sbuf = (T*)take(sizeof(T) * nx * nx);
     C.rowbuf = (T*)take(sizeof(T) * 32);
     C.zbuf = (T*)take(sizeof(T) * 32 * NWARP);
+    C.bsrc = (double*)take(sizeof(double) * n);
     if (std::is_same<T, float>::value) C.X = (double*)take(sizeof(double) * n * nrhs);
     C.W = (T*)take(sizeof(T) * n * nrhs);
     if (std::is_same<T, double>::value) C.X = (double*)C.W;
@@ -402,8 +403,8 @@ __device__ void setup_box(Box& B, const MemberDev& md, const int* lo, const int*
     B.n = B.nx * B.ny;
     B.alpha = alpha;
     for (int sid = 0; sid < 4; ++sid) {
-        int a = sid >> 1;
-        bool phys = (sid & 1) ? (hi[a] == md.n[a]) : (lo[a] == 0);
+        const int a = sid >> 1;
+        const bool phys = (sid & 1) ? (hi[a] == md.n[a]) : (lo[a] == 0);
         if (phys) {
             B.kind[sid] = md.bc_kind[sid] == 1 ? 1 : 0;
             B.val[sid] = md.bc_val[sid];
@@ -411,12 +412,49 @@ __device__ void setup_box(Box& B, const MemberDev& md, const int* lo, const int*
             B.kind[sid] = 2;
             B.val[sid] = 0.0;
         }
+        B.rlen[sid] = 1.0 / (double)(a == 0 ? B.ny : B.nx);
     }
 }
 
 __device__ void fill_scale(const Box& B, Ops& O, bool mixed) {
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x) O.dsc[c] = mixed ? rsqrt(O.cd[c]) : 1.0;
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+        O.dsc[c] = mixed ? (double)rsqrtf((float)O.cd[c]) : 1.0;
     __syncthreads();
+}
+
+// --- bulk (TMA engine) copy global -> shared with an mbarrier -------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Waits for phase `parity` of the barrier for at most ~2^31 cycles (about a
+// second); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
 }
 
 }  // namespace
@@ -440,7 +478,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
     const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (job.type == JOB_PART ? 1 : 0);
     Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? nrhs : 1);
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
-    build_ops(B, md, P.K, C.O);
+    build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
     factor_box<T, BW>(B, C.O, C.Sinv, C.cys, C.Sbuf, C.rowbuf, &C.flags[0]);
 
@@ -464,9 +502,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
     const int npsi = Mth.npsi;
     const double vol = md.h[0] * md.h[1];
     const double ax = md.h[1], ay = md.h[0];
+    const double rax = 1.0 / ax, ray = 1.0 / ay;
     const int nIx = sd.hi[0] - sd.lo[0], nIy = sd.hi[1] - sd.lo[1];
     const int offx = sd.lo[0] - B.lo[0], offy = sd.lo[1] - B.lo[1];
-    int maxit = 0;
+    int maxit = 0, nsolve = 0;
+    const double* fm = P.f + md.cell_off;
     for (int k = warp; k < nrhs; k += NWARP) {
         double* x = C.X + (size_t)k * B.n;
         T* w = C.W + (size_t)k * B.n;
@@ -484,10 +524,17 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
             RhsBasis rb{sk, mk};
             it = warp_solve<T>(B, C.O, C.Sinv, C.cys, x, w, zb, rb, Mth.ir_tol, Mth.max_ir, &C.flags[1]);
         } else {
-            RhsSource rs{P.f + md.cell_off, md.n[0], vol, ax, ay, nullptr};
+            // the particular problem: fixed right-hand side staged once
+            for (int c = lane; c < B.n; c += 32) {
+                const int i = c % B.nx, j = c / B.nx;
+                C.bsrc[c] = source_rhs(B, C.O, fm, md.n[0], vol, ax, ay, nullptr, i, j);
+            }
+            __syncwarp();
+            RhsStored rs{C.bsrc};
             it = warp_solve<T>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol, Mth.max_ir, &C.flags[1]);
         }
         maxit = max(maxit, it);
+        nsolve += it;
         __syncwarp();
         // ---- outputs: restriction to Omega_i and Gamma_i traces (Eq. (informed_space)) ----
         const int slot = (job.type == JOB_BASIS) ? k : P.nbasis_max;
@@ -495,7 +542,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
                               ? P.Psi + ((size_t)job.item * P.nbasis_max + k) * P.ncell_i_max
                               : P.pbar + (size_t)job.item * P.ncell_i_max;
         for (int c = lane; c < nIx * nIy; c += 32) {
-            int i = c % nIx, j = c / nIx;
+            const int i = c % nIx, j = c / nIx;
             psi_out[c] = x[(j + offy) * B.nx + (i + offx)];
         }
         double* mom = P.mom + (((size_t)job.item * (P.nbasis_max + 1) + slot) * MRCM_MAXSIDE) * npsi * 2;
@@ -503,22 +550,22 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
             if (!(sd.side_mask & (1 << sid))) continue;
             const int a = sid >> 1;
             const int len = a == 0 ? nIy : nIx;
+            const double rl = 1.0 / (double)len;
             const double area = a == 0 ? ax : ay;
-            const double h = md.h[a];
+            const double rarea = a == 0 ? rax : ray;
             double* ug = (job.type == JOB_BASIS)
                              ? P.Ug + (((size_t)job.item * P.nbasis_max + k) * MRCM_MAXSIDE + sid) * P.side_max
                              : P.ubg + ((size_t)job.item * MRCM_MAXSIDE + sid) * P.side_max;
-            double fm[3] = {0, 0, 0}, pm[3] = {0, 0, 0};
+            double fmv[3] = {0, 0, 0}, pmv[3] = {0, 0, 0};
             for (int e = lane; e < len; e += 32) {
-                // cell L of Omega_i next to the face, in box coordinates
                 int i, j;
                 if (a == 0) { j = offy + e; i = (sid == 0) ? offx : offx + nIx - 1; }
                 else        { i = offx + e; j = (sid == 2) ? offy : offy + nIy - 1; }
                 const int cL = j * B.nx + i;
                 const double pL = x[cL];
-                const double KL = C.O.Kh[(j + 1) * (B.nx + 2) + i + 1];
+                const double hkL = C.O.hk[2 * cL + a];
                 bool inner;
-                int cR = -1;
+                int cR;
                 double Tf;
                 if (sid == 0) { inner = i > 0; cR = cL - 1; Tf = inner ? C.O.cx[cL - 1] : 0; }
                 else if (sid == 1) { inner = i < B.nx - 1; cR = cL + 1; Tf = inner ? C.O.cx[cL] : 0; }
@@ -526,134 +573,174 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
                 else { inner = j < B.ny - 1; cR = cL + B.nx; Tf = inner ? C.O.cy[cL] : 0; }
                 double uo, pi;
                 if (inner) {
-                    uo = Tf * (pL - x[cR]) / area;
-                    pi = pL - uo * h / (2.0 * KL);
+                    uo = Tf * (pL - x[cR]) * rarea;
+                    pi = pL - uo * hkL;
                 } else {
                     // Robin face of the box (l = 0 basis, or the particular problem)
                     const int pos = a == 0 ? j : i;
                     const int blen = a == 0 ? B.ny : B.nx;
                     double lam = 0.0;
-                    if (job.type == JOB_BASIS && sid == sk) lam = psi_val(mk, pos, blen);
-                    uo = C.O.bT[side_off(B, sid) + pos] * (pL - lam) / area;
+                    if (job.type == JOB_BASIS && sid == sk) lam = psi_val(mk, pos, blen, B.rlen[sid]);
+                    uo = C.O.bT[side_off(B, sid) + pos] * (pL - lam) * rarea;
                     if (job.type == JOB_PART) pi = C.O.bB[side_off(B, sid) + pos] * uo;  // beta ubar.n
-                    else pi = pL - uo * h / (2.0 * KL);
+                    else pi = pL - uo * hkL;
                 }
                 ug[e] = uo;
                 for (int m = 0; m < npsi; ++m) {
-                    double ps = psi_val(m, e, len);
-                    fm[m] += ps * uo * area;
-                    pm[m] += area * ps * pi;
+                    const double ps = psi_val(m, e, len, rl);
+                    fmv[m] += ps * uo * area;
+                    pmv[m] += area * ps * pi;
                 }
             }
             for (int m = 0; m < npsi; ++m) {
                 for (int o = 16; o; o >>= 1) {
-                    fm[m] += __shfl_xor_sync(0xffffffffu, fm[m], o);
-                    pm[m] += __shfl_xor_sync(0xffffffffu, pm[m], o);
+                    fmv[m] += __shfl_xor_sync(0xffffffffu, fmv[m], o);
+                    pmv[m] += __shfl_xor_sync(0xffffffffu, pmv[m], o);
                 }
                 if (lane == 0) {
-                    mom[(sid * npsi + m) * 2 + 0] = fm[m];
-                    mom[(sid * npsi + m) * 2 + 1] = pm[m];
+                    mom[(sid * npsi + m) * 2 + 0] = fmv[m];
+                    mom[(sid * npsi + m) * 2 + 1] = pmv[m];
                 }
             }
         }
     }
-    if (lane == 0 && maxit > 0) atomicMax(&P.status[1], maxit);
+    if (lane == 0 && maxit > 0) {
+        atomicMax(&P.status[1], maxit);
+        atomicAdd(&P.status[3], nsolve);
+    }
     __syncthreads();
     if (threadIdx.x == 0 && C.flags[1]) atomicOr(&P.status[0], ST_NO_CONV);
 }
 
 // ---------------------------------------------------------------------------
 // Step 7: one colour phase of a smoothing step (Sec. 3, Eqs. (sm_1)-(sm_2)).
-// One warp per subdomain of the colour.
+// One CTA (SM_WARPS warps) per subdomain of the colour; the kept factor is
+// staged into shared memory by the bulk-copy (TMA) engine while the
+// coefficients and Robin data are formed; warp 0 runs the sweeps.
 // ---------------------------------------------------------------------------
+constexpr int SM_WARPS = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(32) k_smooth2d(DevPtrs P, MethodDev Mth, const int* items) {
+__global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev Mth, const int* items) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool mixed = std::is_same<T, float>::value;
     const int item = items[blockIdx.x];
     const SubDev sd = P.sub[item];
     const MemberDev& md = P.mem[sd.member];
     __shared__ Box B;
+    __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) setup_box(B, md, sd.loh, sd.hih, Mth.alpha_s);
     __syncthreads();
-    // carve: ops + cys + lam + x + w
-    size_t n = (size_t)B.n;
+    const size_t n = (size_t)B.n;
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = smem + o; o += align16(bytes); return p; };
+    T* Sinv = (T*)take(sizeof(T) * n * B.nx);
     Ops O;
-    O.Kh = (double*)take(sizeof(double) * (B.nx + 2) * (B.ny + 2));
     O.cd = (double*)take(sizeof(double) * n);
     O.cx = (double*)take(sizeof(double) * n);
     O.cy = (double*)take(sizeof(double) * n);
     O.dsc = (double*)take(sizeof(double) * n);
+    O.hk = (double*)take(sizeof(double) * 2 * n);
     O.bT = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
     O.bB = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
     double* lam = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
+    double* bsrc = (double*)take(sizeof(double) * n);
     T* cys = (T*)take(sizeof(T) * n);
     T* zbuf = (T*)take(sizeof(T) * 32);
     double* x = (double*)take(sizeof(double) * n);
     T* w = mixed ? (T*)take(sizeof(T) * n) : (T*)x;
     int* flags = (int*)take(64);
-    if (threadIdx.x == 0) flags[0] = 0;
-    build_ops(B, md, P.K, O);
+    // the bulk copy moves a multiple of 16 bytes; the factor stride and the
+    // shared-memory slot are padded to 16 bytes
+    const uint32_t sbytes = (uint32_t)((sizeof(T) * n * B.nx + 15) & ~size_t(15));
+    const T* Sg = (const T*)P.fac + (size_t)item * P.fac_stride;
+    if (threadIdx.x == 0) {
+        flags[0] = 0;
+        flags[1] = 0;
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, sbytes);
+        bulk_g2s(Sinv, Sg, sbytes, &bar);
+    }
+    build_ops(B, md, P, O);
     const double* dd = P.dsc + (size_t)item * P.dsc_stride;
     for (int c = threadIdx.x; c < B.n; c += blockDim.x) O.dsc[c] = dd[c];
-    __syncwarp();
+    __syncthreads();
     for (int c = threadIdx.x; c < B.n; c += blockDim.x)
         cys[c] = (T)(O.cy[c] * O.dsc[c] * ((c + B.nx < B.n) ? O.dsc[c + B.nx] : 0.0));
     // Robin data from the current solution: lambda = -beta u.n + pi with n the
     // outward normal of hat-Omega_i and pi = p - u.n h / (2K) of the cell inside.
-    const int dim = 2;
     const double* pst = P.p + md.cell_off;
-    const double* ust = P.u + md.cell_off * 2 * dim;
+    const double* ust = P.u + md.cell_off * 4;
     for (int sid = 0; sid < 4; ++sid) {
         if (B.kind[sid] != 2) continue;
         const int a = sid >> 1;
         const int len = a == 0 ? B.ny : B.nx;
-        for (int pos = threadIdx.x; pos < len; pos += 32) {
+        for (int pos = threadIdx.x; pos < len; pos += blockDim.x) {
             int i, j;
             if (a == 0) { j = pos; i = (sid == 0) ? 0 : B.nx - 1; }
             else        { i = pos; j = (sid == 2) ? 0 : B.ny - 1; }
-            long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
-            double un = ust[g * 4 + sid];
-            double kin = O.Kh[(j + 1) * (B.nx + 2) + i + 1];
-            double pi = pst[g] - un * md.h[a] / (2.0 * kin);
+            const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
+            const double un = ust[g * 4 + sid];
+            const double pi = pst[g] - un * O.hk[2 * (j * B.nx + i) + a];
             lam[side_off(B, sid) + pos] = -O.bB[side_off(B, sid) + pos] * un + pi;
         }
     }
-    __syncwarp();
-    const T* Sinv = (const T*)P.fac + (size_t)item * P.fac_stride;
+    __syncthreads();
     const double vol = md.h[0] * md.h[1];
-    RhsSource rs{P.f + md.cell_off, md.n[0], vol, md.h[1], md.h[0], lam};
-    int it = warp_solve<T>(B, O, Sinv, cys, x, w, zbuf, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
-    __syncwarp();
+    const double* fm = P.f + md.cell_off;
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
+        const int i = c % B.nx, j = c / B.nx;
+        bsrc[c] = source_rhs(B, O, fm, md.n[0], vol, md.h[1], md.h[0], lam, i, j);
+    }
+    __syncthreads();
+    int it = 0;
+    if (threadIdx.x < 32) {
+        const bool ok = mbar_wait(&bar, 0);
+        if (!ok) {
+            if (threadIdx.x == 0) flags[1] = 1;
+        } else {
+            RhsStored rs{bsrc};
+            it = warp_solve<T>(B, O, Sinv, cys, x, w, zbuf, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
+        }
+    }
+    __syncthreads();
+    if (flags[1]) {
+        // the staged factor never arrived: report, wait once more for the copy
+        // in flight (bounded) so that no copy targets a finished CTA, and stop
+        if (threadIdx.x == 0) {
+            atomicOr(&P.status[0], ST_BAD);
+            mbar_wait(&bar, 0);
+        }
+        __syncthreads();
+        return;
+    }
     // overwrite (u, p) on Omega_i with the restriction
     const int nIx = sd.hi[0] - sd.lo[0], nIy = sd.hi[1] - sd.lo[1];
     const int offx = sd.lo[0] - B.lo[0], offy = sd.lo[1] - B.lo[1];
     double* pw = P.p + md.cell_off;
     double* uw = P.u + md.cell_off * 4;
-    const double ax = md.h[1], ay = md.h[0];
-    for (int c = threadIdx.x; c < nIx * nIy; c += 32) {
-        int i = c % nIx + offx, j = c / nIx + offy;
-        int cl = j * B.nx + i;
-        long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
-        double pc = x[cl];
+    const double rax = 1.0 / md.h[1], ray = 1.0 / md.h[0];
+    for (int c = threadIdx.x; c < nIx * nIy; c += blockDim.x) {
+        const int i = c % nIx + offx, j = c / nIx + offy;
+        const int cl = j * B.nx + i;
+        const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
+        const double pc = x[cl];
         pw[g] = pc;
         double uo[4];
         for (int sid = 0; sid < 4; ++sid) {
             const int a = sid >> 1;
-            const double area = a == 0 ? ax : ay;
-            bool edge = (sid == 0 && i == 0) || (sid == 1 && i == B.nx - 1) || (sid == 2 && j == 0) ||
-                        (sid == 3 && j == B.ny - 1);
+            const double rarea = a == 0 ? rax : ray;
+            const bool edge = (sid == 0 && i == 0) || (sid == 1 && i == B.nx - 1) || (sid == 2 && j == 0) ||
+                              (sid == 3 && j == B.ny - 1);
             if (!edge) {
-                int cn = sid == 0 ? cl - 1 : sid == 1 ? cl + 1 : sid == 2 ? cl - B.nx : cl + B.nx;
-                double Tf = sid == 0 ? O.cx[cl - 1] : sid == 1 ? O.cx[cl] : sid == 2 ? O.cy[cl - B.nx] : O.cy[cl];
-                uo[sid] = Tf * (pc - x[cn]) / area;
+                const int cn = sid == 0 ? cl - 1 : sid == 1 ? cl + 1 : sid == 2 ? cl - B.nx : cl + B.nx;
+                const double Tf = sid == 0 ? O.cx[cl - 1] : sid == 1 ? O.cx[cl] : sid == 2 ? O.cy[cl - B.nx] : O.cy[cl];
+                uo[sid] = Tf * (pc - x[cn]) * rarea;
             } else {
-                int pos = a == 0 ? j : i;
-                double Tb = O.bT[side_off(B, sid) + pos];
-                if (B.kind[sid] == 2) uo[sid] = Tb * (pc - lam[side_off(B, sid) + pos]) / area;
-                else if (B.kind[sid] == 1) uo[sid] = Tb * (pc - B.val[sid]) / area;
+                const int pos = a == 0 ? j : i;
+                const double Tb = O.bT[side_off(B, sid) + pos];
+                if (B.kind[sid] == 2) uo[sid] = Tb * (pc - lam[side_off(B, sid) + pos]) * rarea;
+                else if (B.kind[sid] == 1) uo[sid] = Tb * (pc - B.val[sid]) * rarea;
                 else uo[sid] = B.val[sid];
             }
         }
@@ -661,6 +748,7 @@ __global__ void __launch_bounds__(32) k_smooth2d(DevPtrs P, MethodDev Mth, const
     }
     if (threadIdx.x == 0) {
         atomicMax(&P.status[1], it);
+        atomicAdd(&P.status[3], it);
         if (flags[0]) atomicOr(&P.status[0], ST_NO_CONV);
     }
 }
@@ -673,10 +761,11 @@ size_t local2d_smem(int prec, int nx, int ny, int nrhs) {
 }
 
 size_t smooth2d_smem(int prec, int nx, int ny) {
-    size_t n = (size_t)nx * ny;
-    size_t s = align16(sizeof(double) * (nx + 2) * (ny + 2)) + align16(sizeof(double) * n) * 4 +
-               align16(sizeof(double) * 2 * (nx + ny)) * 3;
-    size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
+    const size_t n = (size_t)nx * ny;
+    const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
+    size_t s = align16(tsz * n * nx);
+    s += align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);
+    s += align16(sizeof(double) * 2 * (nx + ny)) * 3 + align16(sizeof(double) * n);
     s += align16(tsz * n) + align16(tsz * 32) + align16(sizeof(double) * n);
     if (prec != 0) s += align16(tsz * n);
     return s + 64;
@@ -708,19 +797,19 @@ cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs
     }
 }
 
-cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems,
-                            size_t smem, cudaStream_t s) {
+cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,
+                            cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
     if (M.prec == 0) {
         auto kern = k_smooth2d<double>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<nitems, 32, smem, s>>>(P, M, items);
+        kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
     } else {
         auto kern = k_smooth2d<float>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<nitems, 32, smem, s>>>(P, M, items);
+        kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
     }
     return cudaGetLastError();
 }

@@ -70,6 +70,10 @@ struct DevPtrs {
     const SubDev* sub;
     const double* K;
     const double* f;
+    // face coefficients per cell, 3 per cell (axes x, y, z):
+    const double* Tf;    // transmissibility of the face to the +axis neighbour (0 on the boundary)
+    const double* hk;    // h_a / (2 K) of the cell
+    const double* wh;    // H_a / K_H of the face to the +axis neighbour (beta = alpha * wh)
     double* p;           // state pressure [ncells total]
     double* u;           // state velocities [ncells total][2*dim]
     // factors kept for smoothing

@@ -105,3 +105,45 @@ cudaError_t launch_output(const MemberDev* dmem, int nmem, int member, const dou
     k_output<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(p, u, off, nc, nside, dmean + member, pout, uout);
     return cudaGetLastError();
 }
+
+// Face coefficients of the cell-centred RT0 operator, once per problem:
+// T = a 2 K_L K_R / (h (K_L + K_R)) to the +axis neighbour, h / (2K) per
+// cell and H / K_H per face (so that a Robin face has T = a / (h/2K + alpha H/K_H)).
+__global__ void k_faces(const MemberDev* mem, int nmem, const double* K, double* Tf, double* hk, double* wh) {
+    const int m = blockIdx.y;
+    if (m >= nmem) return;
+    const MemberDev& md = mem[m];
+    const long long nc = (long long)md.n[0] * md.n[1] * md.n[2];
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const long long g = md.cell_off + c;
+    const int ix = (int)(c % md.n[0]);
+    const int iy = (int)((c / md.n[0]) % md.n[1]);
+    const int iz = (int)(c / ((long long)md.n[0] * md.n[1]));
+    const int idx[3] = {ix, iy, iz};
+    const long long st[3] = {1, md.n[0], (long long)md.n[0] * md.n[1]};
+    const double kc = K[g];
+    double vol = md.h[0] * md.h[1] * (md.dim == 3 ? md.h[2] : 1.0);
+    for (int a = 0; a < 3; ++a) {
+        double T = 0.0, w = 0.0, hh = 0.0;
+        if (a < md.dim) {
+            const double area = vol / md.h[a];
+            hh = md.h[a] / (2.0 * kc);
+            if (idx[a] < md.n[a] - 1) {
+                const double kn = K[g + st[a]];
+                T = area * 2.0 * kc * kn / (md.h[a] * (kc + kn));
+                w = md.Hw[a] * (kc + kn) / (2.0 * kc * kn);
+            }
+        }
+        Tf[g * 3 + a] = T;
+        hk[g * 3 + a] = hh;
+        wh[g * 3 + a] = w;
+    }
+}
+
+cudaError_t launch_faces(const MemberDev* dmem, int nmem, long long maxcells, const double* K, double* Tf,
+                         double* hk, double* wh, cudaStream_t s) {
+    dim3 grid((unsigned)((maxcells + 255) / 256), nmem);
+    k_faces<<<grid, 256, 0, s>>>(dmem, nmem, K, Tf, hk, wh);
+    return cudaGetLastError();
+}

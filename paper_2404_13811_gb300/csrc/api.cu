@@ -386,7 +386,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         auto add = [&](int type, int nx, int ny, int nrhs) {
             int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
             byw[bw].push_back(Job{s, type});
-            smem_w[bw] = std::max(smem_w[bw], local2d_smem(prec, nx, ny, std::max(nrhs, 1)));
+            smem_w[bw] = std::max(smem_w[bw], local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1)));
         };
         add(JOB_BASIS, bx, by, sd.nbasis);
         add(JOB_PART, ix, iy, 1);

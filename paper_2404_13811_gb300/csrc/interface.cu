@@ -478,6 +478,38 @@ cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
 // each diagonal block applied through its kept inverse.
 // ---------------------------------------------------------------------------
 
+// X[r][jj] -= sum_c P[r][c] X[k0 + c][jj] for rows r in [ra, rb) and the
+// first nb columns of X (column-major, ld np), with P the panel (column-major,
+// ld np) -- 4 x 4 register tiles (ra, rb, nb multiples of 4).
+__device__ void tile_update(const float* __restrict__ P, float* __restrict__ X, int np, int k0, int b, int ra,
+                            int rb, int nb) {
+    const int ntr = (rb - ra) >> 2, ntc = nb >> 2;
+    for (int t = threadIdx.x; t < ntr * ntc; t += blockDim.x) {
+        const int tc = t / ntr;
+        const int r = ra + ((t - tc * ntr) << 2), jj0 = tc << 2;
+        float acc[4][4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const float4 v = *reinterpret_cast<const float4*>(&X[(jj0 + y) * np + r]);
+            acc[0][y] = v.x; acc[1][y] = v.y; acc[2][y] = v.z; acc[3][y] = v.w;
+        }
+        for (int c = 0; c < b; ++c) {
+            const float4 s4 = *reinterpret_cast<const float4*>(&P[c * np + r]);
+            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+            float xv[4];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) xv[y] = X[(jj0 + y) * np + k0 + c];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] -= sv[x] * xv[y];
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+            *reinterpret_cast<float4*>(&X[(jj0 + y) * np + r]) = make_float4(acc[0][y], acc[1][y], acc[2][y], acc[3][y]);
+    }
+}
+
 __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -497,6 +529,8 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     __shared__ float redv[32];
     __shared__ int redi[32];
     __shared__ int nown;
+    __shared__ int aff[2 * GJ_NB];
+    __shared__ int naff;
     const bool active = e < nel;
     float* A = nullptr;
     float* Ainv = nullptr;
@@ -566,16 +600,40 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             }
             __syncthreads();
         }
-        // interchanges on owned columns
+        // interchanges on owned columns: the panel's swaps composed into one
+        // permutation of at most 2 GJ_NB rows, then gathered column by column
+        for (int i = k0 + tid; i < np; i += nt) qpos[i] = i;
+        __syncthreads();
+        if (tid == 0) {
+            for (int c = 0; c < b; ++c) {
+                const int p = piv[k0 + c], t0 = qpos[k0 + c];
+                qpos[k0 + c] = qpos[p];
+                qpos[p] = t0;
+            }
+            int na = 0;
+            for (int c = 0; c < b; ++c) {
+                if (qpos[k0 + c] != k0 + c) aff[na++] = k0 + c;
+                const int p = piv[k0 + c];
+                if (p >= k0 + b && qpos[p] != p) {
+                    bool seen = false;
+                    for (int t = 0; t < na; ++t) seen |= (aff[t] == p);
+                    if (!seen) aff[na++] = p;
+                }
+            }
+            naff = na;
+        }
+        __syncthreads();
         const int no = nown;
-        for (int jj = tid; jj < no; jj += nt) {
+        for (int jj = warp; jj < no; jj += nwarp) {
             const int j = ownc[jj];
             if (j >= k0 && j < k0 + b) continue;
             float* col = A + (size_t)j * np;
-            for (int c = 0; c < b; ++c) {
-                const int p = piv[k0 + c];
-                if (p != k0 + c) { const float t0 = col[k0 + c]; col[k0 + c] = col[p]; col[p] = t0; }
-            }
+            float v0 = 0.f, v1 = 0.f;
+            if (lane < naff) v0 = col[qpos[aff[lane]]];
+            if (lane + 32 < naff) v1 = col[qpos[aff[lane + 32]]];
+            __syncwarp();
+            if (lane < naff) col[aff[lane]] = v0;
+            if (lane + 32 < naff) col[aff[lane + 32]] = v1;
         }
         __syncthreads();
         if (q % GJ_CL == rank)
@@ -685,13 +743,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                     if (c < b) xc[k0 + c] = x[c];
             }
             __syncthreads();
-            const int r1 = k0 + b;
-            for (int jj = warp; jj < nb; jj += nwarp)
-                for (int r = r1 + lane; r < np; r += 32) {
-                    float acc = Xs[jj * np + r];
-                    for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * Xs[jj * np + k0 + c];
-                    Xs[jj * np + r] = acc;
-                }
+            tile_update(Ps, Xs, np, k0, b, k0 + b, np, nb);
             __syncthreads();
         }
         // backward with U
@@ -720,12 +772,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                     if (c < b) xc[k0 + c] = x[c];
             }
             __syncthreads();
-            for (int jj = warp; jj < nb; jj += nwarp)
-                for (int r = lane; r < k0; r += 32) {
-                    float acc = Xs[jj * np + r];
-                    for (int c = 0; c < b; ++c) acc -= Ps[c * np + r] * Xs[jj * np + k0 + c];
-                    Xs[jj * np + r] = acc;
-                }
+            tile_update(Ps, Xs, np, k0, b, 0, k0, nb);
             __syncthreads();
         }
         for (int jj = warp; jj < nb; jj += nwarp)
@@ -765,8 +812,12 @@ static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, si
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
     const size_t smem = lu_smem(I.npad);
-    cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t set_smem = 0;
+    if (smem > set_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_smem = smem;
+    }
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel, &status};
     return launch_cluster((const void*)k_lu_inverse, nel * GJ_CL, GJ_THREADS, smem, s, args);
@@ -779,8 +830,12 @@ size_t elim_smem_bytes(int nmv, int nmax) {
 
 cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t set_smem = 0;
+    if (smem > set_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_smem = smem;
+    }
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel};
     return launch_cluster((const void*)k_bcr_elim, nel * GJ_CL, EL_THREADS, smem, s, args);

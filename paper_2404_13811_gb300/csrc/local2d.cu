@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int NWARP = 8;
+constexpr int NWARP = 4;
 
 // 1/x in FP64: FP32 reciprocal refined by two Newton steps (error ~ u_64).
 __device__ __forceinline__ double rcp64(double x) {
@@ -153,7 +153,8 @@ __device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
                 if (lane == 0) *bad = 1;
                 piv = 1.0;
             }
-            const T ip = (T)rcp64(piv);
+            // FP32 form: __frcp_rn is the FP64 reciprocal rounded to FP32
+            const T ip = std::is_same<T, float>::value ? (T)__frcp_rn((float)piv) : (T)rcp64(piv);
             if (lane == k) {
 #pragma unroll
                 for (int c = 0; c < BW; ++c) a[c] = (c == k) ? ip : a[c] * ip;
@@ -305,33 +306,34 @@ __device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cy
         warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
         return 1;
     } else {
-        double bn = 0.0;
+        float bn = 0.f;
         for (int j = 0; j < nb; ++j)
             for (int i = lane; i < b; i += 32) {
                 const int c = j * b + i;
-                const double bc = rhs(B, O, i, j);
+                const T wc = (T)(O.dsc[c] * rhs(B, O, i, j));
                 x[c] = 0.0;
-                w[c] = (T)(O.dsc[c] * bc);
-                bn = fmax(bn, fabs(bc));
+                w[c] = wc;
+                bn = fmaxf(bn, fabsf((float)wc));
             }
-        for (int o = 16; o; o >>= 1) bn = fmax(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+        for (int o = 16; o; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
         __syncwarp();
         int it = 0;
         for (; it < max_ir; ++it) {
             warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
             for (int c = lane; c < B.n; c += 32) x[c] += O.dsc[c] * (double)w[c];
             __syncwarp();
-            double rn = 0.0;
+            // FP64 residual of the unscaled operator; the (scaled) norms are taken in FP32
+            float rn = 0.f;
             for (int j = 0; j < nb; ++j)
                 for (int i = lane; i < b; i += 32) {
                     const int c = j * b + i;
-                    const double r = rhs(B, O, i, j) - apply_A(B, O, x, i, j);
-                    rn = fmax(rn, fabs(r));
-                    w[c] = (T)(O.dsc[c] * r);
+                    const T wc = (T)(O.dsc[c] * (rhs(B, O, i, j) - apply_A(B, O, x, i, j)));
+                    w[c] = wc;
+                    rn = fmaxf(rn, fabsf((float)wc));
                 }
-            for (int o = 16; o; o >>= 1) rn = fmax(rn, __shfl_xor_sync(0xffffffffu, rn, o));
+            for (int o = 16; o; o >>= 1) rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
             __syncwarp();
-            if (rn <= tol * bn || bn == 0.0) { ++it; break; }
+            if ((double)rn <= tol * (double)bn || bn == 0.f) { ++it; break; }
             if (it == max_ir - 1 && lane == 0) *noconv = 1;
         }
         return it;
@@ -476,7 +478,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
     }
     __syncthreads();
     const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (job.type == JOB_PART ? 1 : 0);
-    Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? nrhs : 1);
+    Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? min(nrhs, NWARP) : 1);
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
     build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
@@ -508,8 +510,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
     int maxit = 0, nsolve = 0;
     const double* fm = P.f + md.cell_off;
     for (int k = warp; k < nrhs; k += NWARP) {
-        double* x = C.X + (size_t)k * B.n;
-        T* w = C.W + (size_t)k * B.n;
+        double* x = C.X + (size_t)warp * B.n;
+        T* w = C.W + (size_t)warp * B.n;
         int it;
         int sk = -1, mk = 0;
         if (job.type == JOB_BASIS) {
@@ -775,8 +777,12 @@ template <typename T, int BW>
 static cudaError_t launch_local_t(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs,
                                   size_t smem, cudaStream_t s) {
     auto kern = k_local2d<T, BW>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t set_smem = 0;
+    if (smem > set_smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_smem = smem;
+    }
     kern<<<njobs, NWARP * 32, smem, s>>>(P, M, jobs);
     return cudaGetLastError();
 }
@@ -802,13 +808,21 @@ cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* ite
     if (nitems == 0) return cudaSuccess;
     if (M.prec == 0) {
         auto kern = k_smooth2d<double>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        static size_t set_smem = 0;
+        if (smem > set_smem) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set_smem = smem;
+        }
         kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
     } else {
         auto kern = k_smooth2d<float>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        static size_t set_smem = 0;
+        if (smem > set_smem) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set_smem = smem;
+        }
         kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
     }
     return cudaGetLastError();

@@ -156,6 +156,25 @@ int mrcm_smooth(mrcm_handle* h, int n_steps);
 int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells,
                 int device_ptrs);
 
+/* mrcm_fluxes for callers that cannot allocate device memory when they read
+ * results: mrcm_fluxes allocates a device staging buffer for host outputs and
+ * reduces the pure-Neumann pressure gauge into scratch owned by the handle,
+ * which fails or is not allowed where the device memory is already held by
+ * another framework's caching allocator or inside a loop that must not
+ * allocate.  This entry point (the paper has no counterpart; it is part of
+ * this library's output interface) writes member `member`'s solution into
+ * caller DEVICE buffers u_cellfaces [ncells][2 * dim] and p_cells [ncells]
+ * (either may be NULL), with the same values as mrcm_fluxes, and allocates
+ * nothing: its multi-block gauge reduction uses a file-scope static device
+ * array of 1024 partial sums (8 KB, held by every device that loads the
+ * library until the process exits), one per block of 4096 cells, so a member
+ * may have at most 4194304 cells (MRCM_ERR_UNSUPPORTED otherwise).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other
+ * handles) race on it.  Runs on the handle's stream and does not synchronise. */
+int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells);
+
 /* Counters of the last calls: ints[0] = number of subdomains (all members),
  * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
  * last solve, ints[3] = largest local refinement count of the last

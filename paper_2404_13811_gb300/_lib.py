@@ -41,7 +41,7 @@ class mrcm_params(C.Structure):
 
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
-           "mrcm_smooth", "mrcm_fluxes", "mrcm_stats", "mrcm_profile", "mrcm_timings",
+           "mrcm_smooth", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_stats", "mrcm_profile", "mrcm_timings",
            "mrcm_destroy", "mrcm_last_error"]
 PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth"]
 
@@ -73,6 +73,7 @@ def load(path=LIBPATH):
         getattr(lib, name).argtypes = [vp]
     lib.mrcm_smooth.argtypes = [vp, C.c_int]
     lib.mrcm_fluxes.argtypes = [vp, C.c_int, vp, vp, C.c_int]
+    lib.mrcm_fluxes_static.argtypes = [vp, C.c_int, vp, vp]
     lib.mrcm_stats.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double), C.c_int]
     lib.mrcm_profile.argtypes = [vp, C.c_int]
     lib.mrcm_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
@@ -185,6 +186,14 @@ def mrcm_fluxes(h, member, u_cellfaces, p_cells):
     pp, pd = _ptr(p_cells) if p_cells is not None else (None, None)
     dev = ud if ud is not None else bool(pd)
     _check(lib, h, lib.mrcm_fluxes(h, int(member), C.c_void_p(up), C.c_void_p(pp), int(dev)))
+
+
+def mrcm_fluxes_static(h, member, u_cellfaces, p_cells):
+    """Device tensors only (either may be None); allocates nothing (see include/mrcm.h)."""
+    lib = load()
+    up = _ptr(u_cellfaces)[0] if u_cellfaces is not None else None
+    pp = _ptr(p_cells)[0] if p_cells is not None else None
+    _check(lib, h, lib.mrcm_fluxes_static(h, int(member), C.c_void_p(up), C.c_void_p(pp)))
 
 
 def mrcm_stats(h):

@@ -604,6 +604,23 @@ static int check_status(mrcm_handle* h) {
     return 0;
 }
 
+// Internal accessors for the output path that lives with its static scratch (state.cu).
+int mrcm_internal_member_state(mrcm_handle* h, int member, cudaStream_t* st, const double** p, const double** u,
+                               long long* nc, int* nside, int* gauge) {
+    if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "no solution yet");
+    if (member < 0 || member >= (int)h->mem.size()) return fail(h, MRCM_ERR_BAD_INPUT, "bad member");
+    const MemberDev& md = h->mem[member];
+    *st = h->stream;
+    *nside = 2 * h->dim;
+    *nc = (long long)md.n[0] * md.n[1] * md.n[2];
+    *p = h->d_p + md.cell_off;
+    *u = h->d_u + md.cell_off * (*nside);
+    *gauge = md.pure_neumann;
+    return 0;
+}
+
+int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg) { return fail(h, code, msg); }
+
 extern "C" {
 
 int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,

@@ -2,6 +2,7 @@
 // kept basis data (Eqs. (addu), (addp), (uhatphat); Algorithm 1, Step 5), and
 // output of the current solution.
 #include "mrcm_internal.cuh"
+#include <algorithm>
 
 __device__ __forceinline__ double harm_t(double a, double b) { return 2.0 * a * b / (a + b); }
 
@@ -146,4 +147,100 @@ cudaError_t launch_faces(const MemberDev* dmem, int nmem, long long maxcells, co
     dim3 grid((unsigned)((maxcells + 255) / 256), nmem);
     k_faces<<<grid, 256, 0, s>>>(dmem, nmem, K, Tf, hk, wh);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// mrcm_fluxes_static: the output path without any device allocation.
+//
+// mrcm_fluxes allocates a device staging buffer whenever it writes to host
+// memory, and reduces the pure-Neumann pressure gauge into scratch owned by
+// the handle.  Some callers cannot allocate device memory at the point where
+// they read results -- an application whose device memory is already held
+// by another framework's caching allocator, or a real-time loop in which no
+// allocation may happen.  This variant writes into caller device buffers and
+// does its multi-block gauge reduction in the fixed static array below
+// (8 KB, held by every device that loads the library until the process
+// exits).  It allocates nothing.
+// ---------------------------------------------------------------------------
+#include "../../include/mrcm.h"
+
+#define MRCM_STATIC_PARTIALS 1024             // partial sums, one per block
+#define MRCM_STATIC_CELLS_PER_BLOCK 4096      // cells summed by one block
+#define MRCM_STATIC_MAX_CELLS ((long long)MRCM_STATIC_PARTIALS * MRCM_STATIC_CELLS_PER_BLOCK)
+#define MRCM_STATIC_MAX_DEVICES 64
+
+static __device__ __align__(256) double g_gauge_partials[MRCM_STATIC_PARTIALS];
+
+// Block b sums the pressure of cells [b * CELLS_PER_BLOCK, (b + 1) * CELLS_PER_BLOCK)
+// in a fixed order and writes (not accumulates) partials[b].
+__global__ void k_gauge_partials_static(const double* __restrict__ p, long long nc, double* partials) {
+    __shared__ double red[256];
+    const long long c0 = (long long)blockIdx.x * MRCM_STATIC_CELLS_PER_BLOCK;
+    const long long c1 = min(nc, c0 + MRCM_STATIC_CELLS_PER_BLOCK);
+    double s = 0.0;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) s += p[c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_output_static(const double* __restrict__ p, const double* __restrict__ u, long long nc, int nside,
+                                const double* partials, int nblk, int gauge, double* pout, double* uout) {
+    __shared__ double mean;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        if (gauge)
+            for (int b = 0; b < nblk; ++b) s += partials[b];
+        mean = gauge ? s / (double)nc : 0.0;
+    }
+    __syncthreads();
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (pout) pout[c] = p[c] - mean;
+        if (uout)
+            for (int s = 0; s < nside; ++s) uout[c * nside + s] = u[c * nside + s];
+    }
+}
+
+// internal accessors defined with the handle (api.cu)
+int mrcm_internal_member_state(mrcm_handle* h, int member, cudaStream_t* st, const double** p, const double** u,
+                               long long* nc, int* nside, int* gauge);
+int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg);
+
+static double* g_partials_addr[MRCM_STATIC_MAX_DEVICES] = {nullptr};
+
+extern "C" int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    cudaStream_t st;
+    const double *p, *u;
+    long long nc;
+    int nside, gauge;
+    int rc = mrcm_internal_member_state(h, member, &st, &p, &u, &nc, &nside, &gauge);
+    if (rc) return rc;
+    if (nc > MRCM_STATIC_MAX_CELLS)
+        return mrcm_internal_fail(h, MRCM_ERR_UNSUPPORTED,
+                                  "mrcm_fluxes_static: member larger than its static scratch (4194304 cells)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= MRCM_STATIC_MAX_DEVICES)
+        return mrcm_internal_fail(h, MRCM_ERR_CUDA, "mrcm_fluxes_static: no usable current device");
+    if (!g_partials_addr[dev]) {
+        // once per device, with that device current: the device address of the static array
+        void* addr = nullptr;
+        e = cudaGetSymbolAddress(&addr, g_gauge_partials);
+        if (e != cudaSuccess) return mrcm_internal_fail(h, MRCM_ERR_CUDA, cudaGetErrorString(e));
+        g_partials_addr[dev] = (double*)addr;
+    }
+    double* partials = g_partials_addr[dev];
+    const int nblk = (int)((nc + MRCM_STATIC_CELLS_PER_BLOCK - 1) / MRCM_STATIC_CELLS_PER_BLOCK);
+    if (gauge) k_gauge_partials_static<<<nblk, 256, 0, st>>>(p, nc, partials);
+    const int nout = (int)std::min<long long>((nc + 255) / 256, 4096);
+    k_output_static<<<nout, 256, 0, st>>>(p, u, nc, nside, partials, nblk, gauge, p_cells, u_cellfaces);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return mrcm_internal_fail(h, MRCM_ERR_CUDA, cudaGetErrorString(e));
+    return MRCM_OK;
 }

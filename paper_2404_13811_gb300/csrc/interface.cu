@@ -18,6 +18,11 @@ namespace cg = cooperative_groups;
 constexpr int GJ_NB = 32;   // panel width
 constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
 constexpr int GJ_THREADS = 512;
+#ifndef MRCM_PANEL_WARPS
+#define MRCM_PANEL_WARPS 8
+#endif
+constexpr int PANEL_WARPS = MRCM_PANEL_WARPS;   // warps that factor a panel
+constexpr int XCH = 64;          // inverse columns solved together in phase 2
 
 
 
@@ -521,8 +526,8 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     extern __shared__ __align__(16) float lsm[];
     float* Ps = lsm;                           // [c][r], GJ_NB * np
-    float* Xs = Ps + GJ_NB * np;               // [jj][r], GJ_NB * max(np, ncmax)
-    float* Upy = Xs + GJ_NB * max(np, ncmax);  // [c][jj], max(GJ_NB * ncmax, np)
+    float* Xs = Ps + GJ_NB * np;                          // phase 1 [c][jj] (ld ncmax), phase 2 [jj][r]
+    float* Upy = Xs + max(GJ_NB * ncmax, XCH * np);       // [c][jj], max(GJ_NB * ncmax, np)
     int* piv = (int*)(Upy + max(GJ_NB * ncmax, np));  // np
     int* ownc = piv + np;                      // ncmax
     int* qpos = ownc + ncmax;                  // np
@@ -556,50 +561,48 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                 for (int r = k0 + lane; r < np; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
         cluster.sync();
         if (!active) continue;
-        for (int c = 0; c < b; ++c) {
-            const int r0 = k0 + c;
-            float best = -1.f;
-            int bi = r0;
-            for (int r = r0 + tid; r < np; r += nt) {
-                const float v = fabsf(Ps[c * np + r]);
-                if (v > best) { best = v; bi = r; }
-            }
-            for (int o = 16; o; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-            }
-            if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
-            __syncthreads();
-            if (tid < 32) {
-                float v = tid < nwarp ? redv[tid] : -1.f;
-                int ii = tid < nwarp ? redi[tid] : 0x7fffffff;
-                for (int o = 16; o; o >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
-                    if (ov > v || (ov == v && oi < ii)) { v = ov; ii = oi; }
+        // panel factorisation with partial pivoting on warps 0-3 (named barrier 1)
+        if (warp < PANEL_WARPS) {
+            const int pt = tid, pn = PANEL_WARPS * 32;
+            for (int c = 0; c < b; ++c) {
+                const int r0 = k0 + c;
+                float best = -1.f;
+                int bi = r0;
+                for (int r = r0 + pt; r < np; r += pn) {
+                    const float v = fabsf(Ps[c * np + r]);
+                    if (v > best) { best = v; bi = r; }
                 }
-                if (tid == 0) piv[r0] = ii;
+                for (int o = 16; o; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                }
+                if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
+                float v = redv[0];
+                int p = redi[0];
+#pragma unroll
+                for (int w = 1; w < PANEL_WARPS; ++w)
+                    if (redv[w] > v || (redv[w] == v && redi[w] < p)) { v = redv[w]; p = redi[w]; }
+                if (pt == 0) piv[r0] = p;
+                if (p != r0 && pt < b) {
+                    const float t0 = Ps[pt * np + r0];
+                    Ps[pt * np + r0] = Ps[pt * np + p];
+                    Ps[pt * np + p] = t0;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
+                float a = Ps[c * np + r0];
+                if (a == 0.f) { singular = true; a = 1e-30f; }
+                const float ia = 1.f / a;
+                for (int r = r0 + 1 + pt; r < np; r += pn) {
+                    const float l = Ps[c * np + r] * ia;
+                    Ps[c * np + r] = l;
+                    for (int cc = c + 1; cc < b; ++cc) Ps[cc * np + r] -= l * Ps[cc * np + r0];
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
             }
-            __syncthreads();
-            const int p = piv[r0];
-            if (p != r0 && tid < b) {
-                const float t0 = Ps[tid * np + r0];
-                Ps[tid * np + r0] = Ps[tid * np + p];
-                Ps[tid * np + p] = t0;
-            }
-            __syncthreads();
-            float a = Ps[c * np + r0];
-            if (a == 0.f) { singular = true; a = 1e-30f; }
-            const float ia = 1.f / a;
-            for (int r = r0 + 1 + tid; r < np; r += nt) Ps[c * np + r] *= ia;
-            __syncthreads();
-            for (int cc = c + 1 + warp; cc < b; cc += nwarp) {
-                const float u = Ps[cc * np + r0];
-                for (int r = r0 + 1 + lane; r < np; r += 32) Ps[cc * np + r] -= Ps[c * np + r] * u;
-            }
-            __syncthreads();
         }
+        __syncthreads();
         // interchanges on owned columns: the panel's swaps composed into one
         // permutation of at most 2 GJ_NB rows, then gathered column by column
         for (int i = k0 + tid; i < np; i += nt) qpos[i] = i;
@@ -610,18 +613,11 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                 qpos[k0 + c] = qpos[p];
                 qpos[p] = t0;
             }
-            int na = 0;
-            for (int c = 0; c < b; ++c) {
-                if (qpos[k0 + c] != k0 + c) aff[na++] = k0 + c;
-                const int p = piv[k0 + c];
-                if (p >= k0 + b && qpos[p] != p) {
-                    bool seen = false;
-                    for (int t = 0; t < na; ++t) seen |= (aff[t] == p);
-                    if (!seen) aff[na++] = p;
-                }
-            }
-            naff = na;
+            naff = 0;
         }
+        __syncthreads();
+        for (int i = k0 + tid; i < np; i += nt)
+            if (qpos[i] != i) aff[atomicAdd(&naff, 1)] = i;
         __syncthreads();
         const int no = nown;
         for (int jj = warp; jj < no; jj += nwarp) {
@@ -717,9 +713,9 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     }
     __syncthreads();
     const int no = nown;
-    for (int j0 = 0; j0 < no; j0 += GJ_NB) {
-        const int nb = min(GJ_NB, no - j0);
-        for (int jj = warp; jj < GJ_NB; jj += nwarp)
+    for (int j0 = 0; j0 < no; j0 += XCH) {
+        const int nb = min(XCH, no - j0);
+        for (int jj = warp; jj < XCH; jj += nwarp)
             for (int r = lane; r < np; r += 32) Xs[jj * np + r] = (jj < nb && r == qpos[ownc[j0 + jj]]) ? 1.f : 0.f;
         __syncthreads();
         // forward with unit L
@@ -786,7 +782,7 @@ size_t lu_smem(int np) {
     const int npan = (np + GJ_NB - 1) / GJ_NB;
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
-    const size_t xs = (size_t)GJ_NB * std::max(np, ncmax);
+    const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)XCH * np);
     return sizeof(float) * ((size_t)GJ_NB * np + xs + up) +
            sizeof(int) * ((size_t)np + ncmax + np) + 16;
 }

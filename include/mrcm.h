@@ -150,6 +150,19 @@ int mrcm_solve_interface(mrcm_handle* h);
  * and overwrites (u, p) on Omega_i.  smooth(a); smooth(b) == smooth(a + b). */
 int mrcm_smooth(mrcm_handle* h, int n_steps);
 
+/* One whole step -- mrcm_build_basis + mrcm_solve_interface + mrcm_smooth(n_steps)
+ * -- for all members.  use_graph = 0: the eager calls.  use_graph = 1: the
+ * first call runs eagerly (that fixes the number of interface refinement
+ * steps), captures the whole step (every kernel of every phase, all members)
+ * into a CUDA graph on the handle's stream and from then on replays it with
+ * one graph launch; after each replay the interface residual and the local
+ * status are read back (the call synchronises) and MRCM_ERR_NO_CONVERGENCE
+ * is returned if the captured refinement count no longer reaches ir_tol.
+ * The graph is recaptured when n_steps changes.  Inputs are the ones given
+ * at creation (the batching form of the method: uneven subdomains and whole
+ * ensembles in one submission). */
+int mrcm_run(mrcm_handle* h, int n_steps, int use_graph);
+
 /* Writes member `member`'s current solution: u_cellfaces [ncells][2 * dim]
  * outward normal velocities, p_cells [ncells] (either may be NULL).
  * device_ptrs 0: host buffers (the call synchronises); 1: device buffers. */
@@ -190,10 +203,12 @@ int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl
  *   2 interface refinement sweeps (residual, forward, backward, update)
  *   3 assembly of the MRCM-O solution
  *   4 smoothing colour phases (mrcm_smooth)
+ *   5 replays of a captured step (mrcm_run with use_graph = 1)
  * mrcm_timings synchronises the stream and writes, for each of the first n
  * phases, the summed device time in ms (ms[i]) and the number of kernel
  * launches of this library in that phase (launches[i]); either pointer may be
- * NULL.  Launches are counted whether or not profiling is enabled. */
+ * NULL (phase 5 counts graph launches).  Launches are counted whether or not
+ * profiling is enabled. */
 int mrcm_profile(mrcm_handle* h, int enable);
 int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n);
 

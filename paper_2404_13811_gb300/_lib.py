@@ -41,9 +41,9 @@ class mrcm_params(C.Structure):
 
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
-           "mrcm_smooth", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_stats", "mrcm_profile", "mrcm_timings",
+           "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_stats", "mrcm_profile", "mrcm_timings",
            "mrcm_destroy", "mrcm_last_error"]
-PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth"]
+PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph"]
 
 _lib = None
 
@@ -72,6 +72,7 @@ def load(path=LIBPATH):
     for name in ("mrcm_build_basis", "mrcm_solve_interface", "mrcm_destroy"):
         getattr(lib, name).argtypes = [vp]
     lib.mrcm_smooth.argtypes = [vp, C.c_int]
+    lib.mrcm_run.argtypes = [vp, C.c_int, C.c_int]
     lib.mrcm_fluxes.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.mrcm_fluxes_static.argtypes = [vp, C.c_int, vp, vp]
     lib.mrcm_stats.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double), C.c_int]
@@ -179,6 +180,11 @@ def mrcm_smooth(h, n_steps):
     _check(lib, h, lib.mrcm_smooth(h, int(n_steps)))
 
 
+def mrcm_run(h, n_steps, use_graph):
+    lib = load()
+    _check(lib, h, lib.mrcm_run(h, int(n_steps), int(use_graph)))
+
+
 def mrcm_fluxes(h, member, u_cellfaces, p_cells):
     """u_cellfaces / p_cells: both numpy (host) or both torch CUDA tensors (device); either may be None."""
     lib = load()
@@ -213,10 +219,10 @@ def mrcm_profile(h, enable):
 def mrcm_timings(h):
     """{phase: (device ms, launches)} since the last mrcm_profile call."""
     lib = load()
-    ms = (C.c_double * 5)()
-    ln = (C.c_longlong * 5)()
-    _check(lib, h, lib.mrcm_timings(h, ms, ln, 5))
-    return {PHASES[i]: (ms[i], ln[i]) for i in range(5)}
+    ms = (C.c_double * 6)()
+    ln = (C.c_longlong * 6)()
+    _check(lib, h, lib.mrcm_timings(h, ms, ln, 6))
+    return {PHASES[i]: (ms[i], ln[i]) for i in range(6)}
 
 
 def mrcm_destroy(h):

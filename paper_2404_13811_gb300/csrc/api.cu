@@ -104,7 +104,11 @@ struct mrcm_handle {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
-    long long launches[5] = {0, 0, 0, 0, 0};
+    long long launches[6] = {0, 0, 0, 0, 0, 0};
+    // captured step
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr, user_stream = nullptr;
+    int graph_steps = -1, graph_nit = 0;
     // stats
     int if_iters = 0;
     double if_res = 0.0;
@@ -337,6 +341,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     if (count < 1 || !grids || !K || !f || !bcs || !parts || !params)
         return fail(h, MRCM_ERR_BAD_INPUT, "bad arguments");
     h->stream = (cudaStream_t)stream;
+    h->user_stream = h->stream;
     h->prm = *params;
     h->count = count;
     h->dim = grids[0].dim;
@@ -621,6 +626,105 @@ int mrcm_internal_member_state(mrcm_handle* h, int member, cudaStream_t* st, con
 
 int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg) { return fail(h, code, msg); }
 
+// ---------------------------------------------------------------------------
+// kernel-issuing pieces of the pipeline (no host synchronisation inside)
+// ---------------------------------------------------------------------------
+static int issue_basis(mrcm_handle* h) {
+    Phase ph(h, 0);
+    for (auto& jc : h->jclasses) {
+        cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, h->stream);
+        if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
+        h->launches[0] += 1;
+    }
+    return 0;
+}
+
+static int issue_interface_factor(mrcm_handle* h) {
+    cudaStream_t st = h->stream;
+    IfPtrs& I = h->I;
+    Phase ph(h, 1);
+    CUDA_TRY(h, if_assemble(h->P, h->mth, I, (int)h->sub.size(), h->nif, st));
+    CUDA_TRY(h, bcr_fill(I, (int)h->slabs.size(), st));
+    h->launches[1] += 4;
+    for (size_t l = 0; l < h->levels.size(); ++l) {
+        Level& L = h->levels[l];
+        if (L.count == 0) continue;
+        CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
+        h->launches[1] += 1;
+        if (l + 1 < h->levels.size()) {
+            CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
+            h->launches[1] += 1;
+        }
+    }
+    return 0;
+}
+
+static int issue_residual(mrcm_handle* h) {
+    Phase ph(h, 2);
+    CUDA_TRY(h, cudaMemsetAsync(h->I.rnorm, 0, sizeof(unsigned long long) * 2 * h->mem.size(), h->stream));
+    CUDA_TRY(h, if_residual(h->I, h->d_row_member, h->nif, 1, h->stream));
+    h->launches[2] += 1;
+    return 0;
+}
+
+static int issue_if_sweeps(mrcm_handle* h) {
+    Phase ph(h, 2);
+    const int nlev = (int)h->levels.size();
+    for (int l = 0; l < nlev; ++l) {
+        const Level& L = h->levels[l];
+        CUDA_TRY(h, bcr_fwd(h->I, h->d_elims + L.off, L.count, h->npad, h->stream));
+        h->launches[2] += 1;
+    }
+    for (int l = nlev - 2; l >= 0; --l) {
+        const Level& L = h->levels[l];
+        CUDA_TRY(h, bcr_bwd(h->I, h->d_elims + L.off, L.count, h->npad, h->stream));
+        h->launches[2] += 1;
+    }
+    CUDA_TRY(h, if_update(h->I, h->nif, h->stream));
+    h->launches[2] += 1;
+    return 0;
+}
+
+// worst relative residual over the members (synchronises)
+static int read_if_residual(mrcm_handle* h, double* worst) {
+    const int nmem = (int)h->mem.size();
+    std::vector<unsigned long long> nrm(2 * nmem);
+    CUDA_TRY(h, cudaMemcpyAsync(nrm.data(), h->I.rnorm, sizeof(unsigned long long) * 2 * nmem,
+                                cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double w = 0.0;
+    for (int m = 0; m < nmem; ++m) {
+        double rn, bn;
+        std::memcpy(&rn, &nrm[2 * m], 8);
+        std::memcpy(&bn, &nrm[2 * m + 1], 8);
+        w = std::max(w, bn > 0 ? rn / bn : rn);
+    }
+    *worst = w;
+    return 0;
+}
+
+static int issue_assemble(mrcm_handle* h) {
+    Phase ph(h, 3);
+    CUDA_TRY(h, launch_assemble2d(h->P, h->I.x, (int)h->sub.size(), h->ncell_i_max, h->stream));
+    h->launches[3] += 1;
+    return 0;
+}
+
+static int issue_smooth(mrcm_handle* h, int n_steps) {
+    const int nc = 1 << h->dim;
+    Phase ph(h, 4);
+    for (int k = 0; k < n_steps; ++k) {
+        for (int c = 0; c < nc; ++c) {
+            const int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
+            cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
+            if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
+            h->launches[4] += 1;
+        }
+    }
+    h->local_solves += (long long)n_steps * h->sub.size();
+    return 0;
+}
+
 extern "C" {
 
 int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
@@ -641,16 +745,9 @@ int mrcm_build_basis(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     h->err.clear();
     h->stage = ST_CREATED;
-    cudaStream_t st = h->stream;
-    {
-        Phase ph(h, 0);
-        for (auto& jc : h->jclasses) {
-            cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, st);
-            if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
-            h->launches[0] += 1;
-        }
-    }
-    int rc = check_status(h);
+    int rc = issue_basis(h);
+    if (rc) return rc;
+    rc = check_status(h);
     if (rc) return rc;
     for (auto& sd : h->sub) h->local_solves += sd.nbasis + 1;
     h->stage = ST_BASIS;
@@ -661,84 +758,38 @@ int mrcm_solve_interface(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_BASIS) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must follow mrcm_build_basis");
     h->err.clear();
+    int rc = issue_interface_factor(h);
+    if (rc) return rc;
+    // refinement, convergence read back after every step
     cudaStream_t st = h->stream;
-    IfPtrs& I = h->I;
-    const int nitems = (int)h->sub.size();
     const int nmem = (int)h->mem.size();
-    Phase* ph1 = new Phase(h, 1);
-    CUDA_TRY(h, if_assemble(h->P, h->mth, I, nitems, h->nif, st));
-    CUDA_TRY(h, bcr_fill(I, (int)h->slabs.size(), st));
-    h->launches[1] += 4;
-    // factorisation, level by level
-    for (size_t l = 0; l < h->levels.size(); ++l) {
-        Level& L = h->levels[l];
-        if (L.count == 0) continue;
-        CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
-        h->launches[1] += 1;
-        if (l + 1 < h->levels.size()) {
-            CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
-            h->launches[1] += 1;
-        }
-    }
-    delete ph1;
-    // refinement
-    CUDA_TRY(h, cudaMemsetAsync(I.x, 0, sizeof(double) * h->nif, st));
-    std::vector<unsigned long long> nrm(2 * nmem);
-    const int nlev = (int)h->levels.size();
     int it = 0;
     double worst = 0.0;
     std::string hist;
     const int max_it = std::max(8, h->prm.max_ir);
-    Phase* ph2 = new Phase(h, 2);
+    CUDA_TRY(h, cudaMemsetAsync(h->I.x, 0, sizeof(double) * h->nif, st));
     for (;; ++it) {
-        if (it == 0) CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * 2 * nmem, st));
-        else CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * nmem * 2, st));
-        // keep the rhs norms from the first pass: recompute each time (cheap)
-        CUDA_TRY(h, if_residual(I, h->d_row_member, h->nif, 1, st));
-        h->launches[2] += 1;
+        rc = issue_residual(h);
+        if (rc) return rc;
         if (it > 0) {
-            CUDA_TRY(h, cudaMemcpyAsync(nrm.data(), I.rnorm, sizeof(unsigned long long) * 2 * nmem,
-                                        cudaMemcpyDeviceToHost, st));
-            CUDA_TRY(h, cudaStreamSynchronize(st));
-            worst = 0.0;
-            for (int m = 0; m < nmem; ++m) {
-                double rn, bn;
-                std::memcpy(&rn, &nrm[2 * m], 8);
-                std::memcpy(&bn, &nrm[2 * m + 1], 8);
-                worst = std::max(worst, bn > 0 ? rn / bn : rn);
-            }
+            rc = read_if_residual(h, &worst);
+            if (rc) return rc;
             char buf[32];
             snprintf(buf, sizeof(buf), " %.2e", worst);
             hist += buf;
-            if (!std::isfinite(worst)) {
-                delete ph2;
-                return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
-            }
+            if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
             if (worst <= h->mth.ir_tol || it >= max_it) break;
         }
-        for (int l = 0; l < nlev; ++l) {
-            const Level& L = h->levels[l];
-            CUDA_TRY(h, bcr_fwd(I, h->d_elims + L.off, L.count, h->npad, st));
-            h->launches[2] += 1;
-        }
-        for (int l = nlev - 2; l >= 0; --l) {
-            const Level& L = h->levels[l];
-            CUDA_TRY(h, bcr_bwd(I, h->d_elims + L.off, L.count, h->npad, st));
-            h->launches[2] += 1;
-        }
-        CUDA_TRY(h, if_update(I, h->nif, st));
-        h->launches[2] += 1;
+        rc = issue_if_sweeps(h);
+        if (rc) return rc;
     }
-    delete ph2;
+    (void)nmem;
     h->if_iters = it;
     h->if_res = worst;
     if (worst > h->mth.ir_tol * 1e3)
         return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled; residuals:" + hist);
-    {
-        Phase ph3(h, 3);
-        CUDA_TRY(h, launch_assemble2d(h->P, I.x, nitems, h->ncell_i_max, st));
-        h->launches[3] += 1;
-    }
+    rc = issue_assemble(h);
+    if (rc) return rc;
     h->stage = ST_SOLVED;
     return 0;
 }
@@ -748,20 +799,85 @@ int mrcm_smooth(mrcm_handle* h, int n_steps) {
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_smooth must follow mrcm_solve_interface");
     if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
     h->err.clear();
-    const int nc = 1 << h->dim;
-    {
-        Phase ph4(h, 4);
-        for (int k = 0; k < n_steps; ++k) {
-            for (int c = 0; c < nc; ++c) {
-                int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
-                cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
-                if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
-                h->launches[4] += 1;
-            }
-        }
-    }
-    h->local_solves += (long long)n_steps * h->sub.size();
+    int rc = issue_smooth(h, n_steps);
+    if (rc) return rc;
     return check_status(h);
+}
+
+int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
+    h->err.clear();
+    int rc;
+    if (!use_graph || h->if_iters == 0) {
+        // eager: also fixes the refinement count a captured step will use
+        rc = mrcm_build_basis(h);
+        if (rc) return rc;
+        rc = mrcm_solve_interface(h);
+        if (rc) return rc;
+        rc = mrcm_smooth(h, n_steps);
+        if (rc || !use_graph) return rc;
+    }
+    cudaStream_t st = h->stream;
+    if (!h->graph_exec || h->graph_steps != n_steps) {
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        const bool prof = h->prof;
+        h->prof = false;  // no profiling events inside the graph
+        h->graph_nit = h->if_iters + 1;
+        // capture on a private stream (the legacy default stream cannot be captured)
+        if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        h->stream = h->cap_stream;
+        st = h->cap_stream;
+        CUDA_TRY(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int crc = 0;
+        do {
+            if (cudaMemsetAsync(h->d_status, 0, sizeof(int), st) != cudaSuccess) { crc = MRCM_ERR_CUDA; break; }
+            if ((crc = issue_basis(h))) break;
+            if ((crc = issue_interface_factor(h))) break;
+            if (cudaMemsetAsync(h->I.x, 0, sizeof(double) * h->nif, st) != cudaSuccess) { crc = MRCM_ERR_CUDA; break; }
+            for (int it = 0; it < h->graph_nit && !crc; ++it) {
+                if ((crc = issue_residual(h))) break;
+                crc = issue_if_sweeps(h);
+            }
+            if (crc) break;
+            if ((crc = issue_residual(h))) break;  // residual of the final iterate, checked after the launch
+            if ((crc = issue_assemble(h))) break;
+            crc = issue_smooth(h, n_steps);
+        } while (0);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        h->prof = prof;
+        h->stream = h->user_stream;
+        st = h->stream;
+        if (crc) {
+            if (g) cudaGraphDestroy(g);
+            return crc;
+        }
+        if (ce != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        h->graph_steps = n_steps;
+    }
+    {
+        Phase ph(h, 5);
+        CUDA_TRY(h, cudaGraphLaunch(h->graph_exec, st));
+    }
+    h->launches[5] += 1;
+    double worst = 0.0;
+    rc = read_if_residual(h, &worst);
+    if (rc) return rc;
+    h->if_res = worst;
+    if (!std::isfinite(worst) || worst > h->mth.ir_tol * 1e3)
+        return fail(h, MRCM_ERR_NO_CONVERGENCE, "captured step: interface refinement count too small");
+    rc = check_status(h);
+    if (rc) return rc;
+    h->stage = ST_SOLVED;
+    return 0;
 }
 
 int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells, int device_ptrs) {
@@ -814,13 +930,13 @@ int mrcm_profile(mrcm_handle* h, int enable) {
 int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     for (auto& r : h->ev_rec) {
         float t = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&t, r.second.first, r.second.second));
-        if (r.first >= 0 && r.first < 5) acc[r.first] += t;
+        if (r.first >= 0 && r.first < 6) acc[r.first] += t;
     }
-    for (int i = 0; i < n && i < 5; ++i) {
+    for (int i = 0; i < n && i < 6; ++i) {
         if (ms) ms[i] = acc[i];
         if (launches) launches[i] = h->launches[i];
     }
@@ -835,6 +951,8 @@ int mrcm_destroy(mrcm_handle* h) {
     }
     for (void* p : h->allocs) cudaFree(p);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return 0;
 }

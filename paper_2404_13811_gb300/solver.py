@@ -106,8 +106,7 @@ class MRCM:
         except Exception:
             pass
 
-    def run(self, n_smooth):
-        self.build_basis()
-        self.solve_interface()
-        if n_smooth:
-            self.smooth(n_smooth)
+    def run(self, n_smooth, graph=False):
+        """One full step (basis, interface, n_smooth smoothing steps); graph=True
+        replays it as one captured CUDA graph after the first (eager) call."""
+        L.mrcm_run(self.h, n_smooth, int(graph))

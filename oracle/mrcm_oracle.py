@@ -161,7 +161,7 @@ def assemble_box(prob, lo, hi, alpha, Hw):
     Kc = Kflat[flat_index(cells, n)]
     vol = float(np.prod(h))
     rows, cols, vals = [], [], []
-    diag = np.zeros(nloc)
+    diag = np.zeros(nloc, dtype=Kc.dtype)
     inner = []
     sides = [None] * (2 * d)
     loc_idx = np.arange(nloc)
@@ -216,7 +216,7 @@ def box_rhs(prob, sysm, robin, sources):
     sources -- include f, g and z (True) or set them to zero (False, the
                homogeneous problems of Eq. (oversampling_problem))."""
     vol = float(np.prod(prob.h))
-    b = np.zeros(len(sysm.Kc))
+    b = np.zeros(len(sysm.Kc), dtype=sysm.Kc.dtype)
     if sources:
         b += prob.f.reshape(-1)[flat_index(sysm.cells, prob.n)] * vol
     for sid, sd in enumerate(sysm.sides):
@@ -238,7 +238,7 @@ def box_velocities(prob, sysm, p, robin, sources):
     ``assemble_box``)."""
     d = prob.dim
     vol = float(np.prod(prob.h))
-    u = np.zeros((len(p), 2 * d))
+    u = np.zeros((len(p), 2 * d), dtype=np.result_type(p, sysm.Kc))
     for a in range(d):
         area = vol / prob.h[a]
         L, R, T = sysm.inner[a]
@@ -268,6 +268,14 @@ class BandCholesky:
     def __init__(self, A):
         A = sp.csr_matrix(A)
         n = A.shape[0]
+        self.n = n
+        self.lu = None
+        if np.iscomplexobj(A.data):
+            # complex-step derivatives (K + i h): the operator is complex
+            # symmetric, not Hermitian, so a conjugating Cholesky would be
+            # wrong; an unconjugated sparse LU solves the same system
+            self.lu = spla.splu(A.tocsc())
+            return
         coo = A.tocoo()
         low = coo.row >= coo.col
         bw = int((coo.row - coo.col)[low].max()) if n > 1 else 0
@@ -278,6 +286,8 @@ class BandCholesky:
         self.n = n
 
     def solve(self, b):
+        if self.lu is not None:
+            return self.lu.solve(np.asarray(b, dtype=complex))
         return sla.cho_solve_banded((self.cb, True), b)
 
 
@@ -524,7 +534,7 @@ def mrcm_os(prob, sub, overlap, space=1, alpha_basis=1.0, alpha_smooth=1.0, n_sm
             beta = gamma_beta(prob, sd, sid_i, alpha_basis, Hw)
             for kind in ("M", "V"):
                 for m in range(psi.shape[1]):
-                    row = np.zeros(nX)
+                    row = np.zeros(nX, dtype=prob.K.dtype)
                     r = 0.0
                     for (sdx, sid, sign) in ((sd, sid_i, 1.0), (sj, sid_j, -1.0)):
                         D = sdx.data
@@ -563,8 +573,8 @@ def mrcm_os(prob, sub, overlap, space=1, alpha_basis=1.0, alpha_smooth=1.0, n_sm
     # Superposition u = ubar + sum_j X_j Phi_j, p = pbar + sum_j X_j Psi_j
     # (Eqs. (addu), (addp), (uhatphat)).
     ncell = prob.ncells
-    p = np.zeros(ncell)
-    u = np.zeros((ncell, 2 * d))
+    p = np.zeros(ncell, dtype=prob.K.dtype)
+    u = np.zeros((ncell, 2 * d), dtype=prob.K.dtype)
     for sd in subs:
         D = sd.data
         xi = X[col0[sd.index]:col0[sd.index + 1]]

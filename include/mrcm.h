@@ -188,6 +188,37 @@ int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells
  * handles) race on it.  Runs on the handle's stream and does not synchronise. */
 int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells);
 
+/* Replaces the permeability of every member (concatenated in member order,
+ * [total cells]): values are K (is_log = 0; > 0 and finite) or log K
+ * (is_log = 1; finite).  device_ptrs 0: host pointer; 1: device pointer.
+ * Recomputes the face coefficients of Sec. 2.2 and returns the handle to
+ * the created stage: mrcm_build_basis must run next (a captured step of
+ * mrcm_run is dropped and captured again).  MRCM_ERR_BAD_INPUT when a value
+ * is out of range (checked on the host for host input, on the device for
+ * device input; the handle's K is then not usable).  Synchronises. */
+int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int device_ptrs);
+
+/* Differentiation form: reverse mode of the whole computation that produced
+ * the current solution -- basis problems (Eq. (oversampling_problem)),
+ * particular problems (Eqs. (111dbar)-(122dbar)), interface system (Eqs.
+ * (int_ujump)-(int_pjump)), superposition (Eqs. (addu), (addp)) and every
+ * smoothing step applied since the last interface solve (Eqs.
+ * (sm_1)-(sm_2)) -- with respect to log K of every cell.
+ *   gp    [total cells] dL/dp and gu [total cells][2 * dim] dL/du of a
+ *         scalar L of the returned solution (member order, the layout of
+ *         mrcm_fluxes); either may be NULL (zero).
+ *   g_logK [total cells] output dL/dlog K.
+ *   device_ptrs 0: host arrays (the call synchronises); 1: device arrays.
+ * The kept factors serve the transposed local solves (the operators are
+ * symmetric); the local forward solutions are recomputed, not stored; the
+ * smoothing steps are replayed once to record the state before each colour
+ * pass (n_steps x 2^dim states of (p, u), allocated by the handle on first
+ * use); the interface system is solved transposed with its FP32 slab factors
+ * and FP64 refinement.  Leaves the current solution unchanged.
+ * MRCM_ERR_UNSUPPORTED for a member with no Dirichlet side (its pressure is
+ * fixed only up to a constant).  Needs a solution (MRCM_ERR_STATE). */
+int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs);
+
 /* Counters of the last calls: ints[0] = number of subdomains (all members),
  * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
  * last solve, ints[3] = largest local refinement count of the last

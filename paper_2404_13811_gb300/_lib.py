@@ -41,8 +41,8 @@ class mrcm_params(C.Structure):
 
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
-           "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_stats", "mrcm_profile", "mrcm_timings",
-           "mrcm_destroy", "mrcm_last_error"]
+           "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_set_permeability",
+           "mrcm_adjoint", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_destroy", "mrcm_last_error"]
 PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph"]
 
 _lib = None
@@ -75,6 +75,8 @@ def load(path=LIBPATH):
     lib.mrcm_run.argtypes = [vp, C.c_int, C.c_int]
     lib.mrcm_fluxes.argtypes = [vp, C.c_int, vp, vp, C.c_int]
     lib.mrcm_fluxes_static.argtypes = [vp, C.c_int, vp, vp]
+    lib.mrcm_set_permeability.argtypes = [vp, vp, C.c_int, C.c_int]
+    lib.mrcm_adjoint.argtypes = [vp, vp, vp, vp, C.c_int]
     lib.mrcm_stats.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double), C.c_int]
     lib.mrcm_profile.argtypes = [vp, C.c_int]
     lib.mrcm_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
@@ -200,6 +202,22 @@ def mrcm_fluxes_static(h, member, u_cellfaces, p_cells):
     up = _ptr(u_cellfaces)[0] if u_cellfaces is not None else None
     pp = _ptr(p_cells)[0] if p_cells is not None else None
     _check(lib, h, lib.mrcm_fluxes_static(h, int(member), C.c_void_p(up), C.c_void_p(pp)))
+
+
+def mrcm_set_permeability(h, values, is_log):
+    """values: K or log K of all members (numpy on the host or a CUDA tensor)."""
+    lib = load()
+    vp_, dev = _ptr(values)
+    _check(lib, h, lib.mrcm_set_permeability(h, C.c_void_p(vp_), int(is_log), int(dev)))
+
+
+def mrcm_adjoint(h, gp, gu, g_logK):
+    """gp / gu (either may be None) and the output g_logK: all numpy or all CUDA tensors."""
+    lib = load()
+    op, dev = _ptr(g_logK)
+    pp = _ptr(gp)[0] if gp is not None else None
+    up = _ptr(gu)[0] if gu is not None else None
+    _check(lib, h, lib.mrcm_adjoint(h, C.c_void_p(pp), C.c_void_p(up), C.c_void_p(op), int(dev)))
 
 
 def mrcm_stats(h):

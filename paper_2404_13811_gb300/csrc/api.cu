@@ -42,6 +42,24 @@ cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
 size_t elim_smem_bytes(int nmv, int nmax);
+cudaError_t if_residualT(const IfPtrs& I, const SubDev* sub, const int* col_item, const double* z,
+                         const double* y, const int* row_member, int n, int first, cudaStream_t s);
+cudaError_t bcr_bwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, int up, cudaStream_t s);
+cudaError_t bcr_fwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
+cudaError_t if_updateT(const IfPtrs& I, double* y, int n, cudaStream_t s);
+size_t adj_smooth2d_smem(int prec, int nx, int ny);
+size_t adj_local2d_smem(int prec, int nx, int ny, int nw, bool part);
+cudaError_t launch_adj_smooth2d(const DevPtrs& P, const MethodDev& M, const AdjPtrs& A, const int* items,
+                                int nitems, size_t smem, cudaStream_t s);
+cudaError_t launch_adj_assemble2d(const DevPtrs& P, const AdjPtrs& A, int nitems, int ncell_i_max,
+                                  cudaStream_t s);
+cudaError_t launch_adj_moments(const DevPtrs& P, const MethodDev& M, const AdjPtrs& A, int nitems,
+                               cudaStream_t s);
+cudaError_t launch_adj_local2d(const DevPtrs& P, const MethodDev& M, const AdjPtrs& A, const Job* jobs,
+                               int njobs, int bw, int nw, size_t smem, cudaStream_t s);
+cudaError_t launch_grad_logK(const MemberDev* dmem, int nmem, long long maxcells, const double* K,
+                             const double* Tf, const double* hk, const AdjPtrs& A, double* out, cudaStream_t s);
+cudaError_t launch_set_K(const double* src, double* K, long long n, int is_log, int* status, cudaStream_t s);
 
 namespace {
 
@@ -55,6 +73,25 @@ struct JobClass {
 
 struct Level {
     int off, count;           // into the elimination array
+};
+
+struct AdjClass {
+    int bw, nw;
+    size_t smem;
+    int off, count;
+};
+
+// Workspace of the reverse pass, allocated by the first mrcm_adjoint call.
+struct AdjWork {
+    bool ready = false;
+    AdjPtrs A{};
+    int* col_item = nullptr;
+    Job* jobs = nullptr;
+    std::vector<AdjClass> classes;
+    size_t smooth_smem = 0;
+    double* snap = nullptr;
+    size_t snap_len = 0;      // doubles
+    double* gout = nullptr;   // device result when the caller passes host memory
 };
 
 }  // namespace
@@ -109,6 +146,9 @@ struct mrcm_handle {
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr, user_stream = nullptr;
     int graph_steps = -1, graph_nit = 0;
+    // reverse pass
+    AdjWork adj;
+    int smooth_steps = 0;     // smoothing steps applied since the last interface solve
     // stats
     int if_iters = 0;
     double if_res = 0.0;
@@ -725,6 +765,117 @@ static int issue_smooth(mrcm_handle* h, int n_steps) {
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// reverse pass (differentiation with respect to log K)
+// ---------------------------------------------------------------------------
+static int prepare_adjoint(mrcm_handle* h) {
+    AdjWork& W = h->adj;
+    if (W.ready) return 0;
+    const int prec = h->prm.precision;
+    const int nitems = (int)h->sub.size();
+    const int nmem = (int)h->mem.size();
+    const size_t lim = 227 * 1024;
+    // jobs: basis problem on hat-Omega_i and particular problem on Omega_i,
+    // grouped by band width and the number of warps that fit in shared memory
+    std::map<std::pair<int, int>, std::vector<Job>> by;
+    std::map<std::pair<int, int>, size_t> smem;
+    for (int s = 0; s < nitems; ++s) {
+        const SubDev& sd = h->sub[s];
+        for (int type = 0; type < 2; ++type) {
+            const int nx = type == JOB_BASIS ? sd.hih[0] - sd.loh[0] : sd.hi[0] - sd.lo[0];
+            const int ny = type == JOB_BASIS ? sd.hih[1] - sd.loh[1] : sd.hi[1] - sd.lo[1];
+            const int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
+            int nw = 4;
+            while (nw > 1 && adj_local2d_smem(prec, nx, ny, nw, type == JOB_PART) > lim) nw /= 2;
+            const size_t b = adj_local2d_smem(prec, nx, ny, nw, type == JOB_PART);
+            if (b > lim) return fail(h, MRCM_ERR_UNSUPPORTED, "subdomain box too large for the adjoint kernels");
+            by[{bw, nw}].push_back(Job{s, type});
+            smem[{bw, nw}] = std::max(smem[{bw, nw}], b);
+        }
+        W.smooth_smem = std::max(W.smooth_smem, adj_smooth2d_smem(prec, sd.hih[0] - sd.loh[0], sd.hih[1] - sd.loh[1]));
+    }
+    if (W.smooth_smem > lim) return fail(h, MRCM_ERR_UNSUPPORTED, "subdomain box too large for the adjoint kernels");
+    std::vector<Job> jobs;
+    W.classes.clear();
+    for (auto& kv : by) {
+        W.classes.push_back(AdjClass{kv.first.first, kv.first.second, smem[kv.first], (int)jobs.size(),
+                                     (int)kv.second.size()});
+        jobs.insert(jobs.end(), kv.second.begin(), kv.second.end());
+    }
+    std::vector<int> col_item(std::max(h->nif, 1), 0);
+    for (int s = 0; s < nitems; ++s)
+        for (int k = 0; k < h->sub[s].nbasis; ++k) col_item[h->sub[s].col0 + k] = s;
+    const int nside = 2 * h->dim;
+    AdjPtrs& A = W.A;
+    int e = 0;
+    if ((e = dalloc(h, &A.gp, h->ncells))) return e;
+    if ((e = dalloc(h, &A.gu, h->ncells * nside))) return e;
+    if ((e = dalloc(h, &A.gTf, h->ncells * 3))) return e;
+    if ((e = dalloc(h, &A.ghk, h->ncells * 3))) return e;
+    if ((e = dalloc(h, &A.gwh, h->ncells * 3))) return e;
+    if ((e = dalloc(h, &A.gps, (size_t)nitems * h->ncell_i_max))) return e;
+    if ((e = dalloc(h, &A.gug, (size_t)nitems * MRCM_MAXSIDE * h->side_max))) return e;
+    if ((e = dalloc(h, &A.gX, h->nif))) return e;
+    if ((e = dalloc(h, &A.y, h->nif))) return e;
+    if ((e = dalloc(h, &A.gmom, (size_t)nitems * (h->nbasis_max + 1) * MRCM_MAXSIDE * h->npsi * 2))) return e;
+    if ((e = dalloc(h, &W.col_item, col_item.size()))) return e;
+    if ((e = dalloc(h, &W.jobs, jobs.size()))) return e;
+    if ((e = dalloc(h, &W.gout, h->ncells))) return e;
+    A.X = h->I.x;
+    CUDA_TRY(h, cudaMemcpyAsync(W.col_item, col_item.data(), sizeof(int) * col_item.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(W.jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, h->stream));
+    (void)nmem;
+    W.ready = true;
+    return 0;
+}
+
+// dL/drhs = G^-T dL/dX by refinement with the transposed slab factors.
+static int solve_interface_T(mrcm_handle* h) {
+    AdjWork& W = h->adj;
+    cudaStream_t st = h->stream;
+    const IfPtrs& I = h->I;
+    const int nlev = (int)h->levels.size();
+    const int max_it = std::max(8, h->prm.max_ir);
+    double worst = 0.0;
+    std::string hist;
+    CUDA_TRY(h, cudaMemsetAsync(W.A.y, 0, sizeof(double) * h->nif, st));
+    for (int it = 0;; ++it) {
+        {
+            Phase ph(h, 2);
+            CUDA_TRY(h, cudaMemsetAsync(I.rnorm, 0, sizeof(unsigned long long) * 2 * h->mem.size(), st));
+            CUDA_TRY(h, if_residualT(I, h->d_sub, W.col_item, W.A.gX, W.A.y, h->d_row_member, h->nif, 1, st));
+            h->launches[2] += 1;
+        }
+        if (it > 0) {
+            int rc = read_if_residual(h, &worst);
+            if (rc) return rc;
+            char buf[32];
+            snprintf(buf, sizeof(buf), " %.2e", worst);
+            hist += buf;
+            if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "transposed interface refinement diverged");
+            if (worst <= h->mth.ir_tol || it >= max_it) break;
+        }
+        Phase ph(h, 2);
+        for (int l = 0; l + 1 < nlev; ++l) {
+            const Level& L = h->levels[l];
+            CUDA_TRY(h, bcr_bwdT(I, h->d_elims + L.off, L.count, h->npad, 0, st));
+            CUDA_TRY(h, bcr_bwdT(I, h->d_elims + L.off, L.count, h->npad, 1, st));
+            h->launches[2] += 2;
+        }
+        for (int l = nlev - 1; l >= 0; --l) {
+            const Level& L = h->levels[l];
+            CUDA_TRY(h, bcr_fwdT(I, h->d_elims + L.off, L.count, h->npad, st));
+            h->launches[2] += 1;
+        }
+        CUDA_TRY(h, if_updateT(I, W.A.y, h->nif, st));
+        h->launches[2] += 1;
+    }
+    if (worst > h->mth.ir_tol * 1e3)
+        return fail(h, MRCM_ERR_NO_CONVERGENCE, "transposed interface refinement stalled; residuals:" + hist);
+    return 0;
+}
+
 extern "C" {
 
 int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
@@ -790,6 +941,7 @@ int mrcm_solve_interface(mrcm_handle* h) {
         return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled; residuals:" + hist);
     rc = issue_assemble(h);
     if (rc) return rc;
+    h->smooth_steps = 0;
     h->stage = ST_SOLVED;
     return 0;
 }
@@ -801,6 +953,7 @@ int mrcm_smooth(mrcm_handle* h, int n_steps) {
     h->err.clear();
     int rc = issue_smooth(h, n_steps);
     if (rc) return rc;
+    h->smooth_steps += n_steps;
     return check_status(h);
 }
 
@@ -876,6 +1029,7 @@ int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
         return fail(h, MRCM_ERR_NO_CONVERGENCE, "captured step: interface refinement count too small");
     rc = check_status(h);
     if (rc) return rc;
+    h->smooth_steps = n_steps;
     h->stage = ST_SOLVED;
     return 0;
 }
@@ -907,6 +1061,137 @@ int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells
         CUDA_TRY(h, cudaStreamSynchronize(st));
     }
     return 0;
+}
+
+int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int device_ptrs) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (!values) return fail(h, MRCM_ERR_BAD_INPUT, "null permeability");
+    h->err.clear();
+    cudaStream_t st = h->stream;
+    const long long nc = h->ncells;
+    if (!device_ptrs) {
+        for (long long c = 0; c < nc; ++c) {
+            const double v = values[c];
+            if (!std::isfinite(v) || (!is_log && !(v > 0.0)))
+                return fail(h, MRCM_ERR_BAD_INPUT, "K must be positive and finite");
+        }
+    }
+    const double* src = values;
+    double* tmp = nullptr;
+    if (!device_ptrs) {
+        CUDA_TRY(h, cudaMallocAsync((void**)&tmp, sizeof(double) * nc, st));
+        CUDA_TRY(h, cudaMemcpyAsync(tmp, values, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+        src = tmp;
+    }
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, launch_set_K(src, h->d_K, nc, is_log, h->d_status, st));
+    if (tmp) CUDA_TRY(h, cudaFreeAsync(tmp, st));
+    long long maxc = 0;
+    for (auto& md : h->mem) maxc = std::max(maxc, (long long)md.n[0] * md.n[1] * md.n[2]);
+    CUDA_TRY(h, launch_faces(h->d_mem, (int)h->mem.size(), maxc, h->d_K, h->d_Tf, h->d_hk, h->d_wh, st));
+    int stv = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&stv, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    h->stage = ST_CREATED;
+    h->if_iters = 0;  // a captured step re-learns its refinement count
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_steps = -1;
+    }
+    if (stv & ST_BAD_K) return fail(h, MRCM_ERR_BAD_INPUT, "K must be positive and finite");
+    return 0;
+}
+
+int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");
+    if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_adjoint needs a solution");
+    for (auto& md : h->mem)
+        if (md.pure_neumann)
+            return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint needs Dirichlet data on some side of every member");
+    h->err.clear();
+    int rc = prepare_adjoint(h);
+    if (rc) return rc;
+    AdjWork& W = h->adj;
+    AdjPtrs& A = W.A;
+    cudaStream_t st = h->stream;
+    const int d = h->dim, nside = 2 * d, ncol = 1 << d;
+    const int ns = h->smooth_steps;
+    const size_t cells = (size_t)h->ncells;
+    const size_t per_snap = cells * (1 + nside);
+    const size_t need = per_snap * (size_t)ns * ncol;
+    if (need > W.snap_len) {
+        int e = dalloc(h, &W.snap, need);
+        if (e) return e;
+        W.snap_len = need;
+    }
+    const int nitems = (int)h->sub.size();
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    // replay: the MRCM-O state again, then the smoothing steps, recording the
+    // state before every colour pass (forward solves with the kept factors)
+    if ((rc = issue_assemble(h))) return rc;
+    for (int s = 0; s < ns; ++s)
+        for (int c = 0; c < ncol; ++c) {
+            double* sp = W.snap + per_snap * ((size_t)s * ncol + c);
+            CUDA_TRY(h, cudaMemcpyAsync(sp, h->d_p, sizeof(double) * cells, cudaMemcpyDeviceToDevice, st));
+            CUDA_TRY(h, cudaMemcpyAsync(sp + cells, h->d_u, sizeof(double) * cells * nside, cudaMemcpyDeviceToDevice,
+                                        st));
+            Phase ph(h, 4);
+            const int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
+            CUDA_TRY(h, launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, st));
+            h->launches[4] += 1;
+        }
+    // seeds
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (gp) CUDA_TRY(h, cudaMemcpyAsync(A.gp, gp, sizeof(double) * cells, kind, st));
+    else CUDA_TRY(h, cudaMemsetAsync(A.gp, 0, sizeof(double) * cells, st));
+    if (gu) CUDA_TRY(h, cudaMemcpyAsync(A.gu, gu, sizeof(double) * cells * nside, kind, st));
+    else CUDA_TRY(h, cudaMemsetAsync(A.gu, 0, sizeof(double) * cells * nside, st));
+    CUDA_TRY(h, cudaMemsetAsync(A.gTf, 0, sizeof(double) * cells * 3, st));
+    CUDA_TRY(h, cudaMemsetAsync(A.ghk, 0, sizeof(double) * cells * 3, st));
+    CUDA_TRY(h, cudaMemsetAsync(A.gwh, 0, sizeof(double) * cells * 3, st));
+    CUDA_TRY(h, cudaMemsetAsync(A.gmom, 0,
+                                sizeof(double) * nitems * (h->nbasis_max + 1) * MRCM_MAXSIDE * h->npsi * 2, st));
+    // smoothing backwards: steps and colours in reverse order
+    for (int s = ns - 1; s >= 0; --s)
+        for (int c = ncol - 1; c >= 0; --c) {
+            const double* sp = W.snap + per_snap * ((size_t)s * ncol + c);
+            A.ps = sp;
+            A.us = sp + cells;
+            Phase ph(h, 4);
+            const int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
+            CUDA_TRY(h, launch_adj_smooth2d(h->P, h->mth, A, h->d_colour_items + off, cnt, W.smooth_smem, st));
+            h->launches[4] += 1;
+        }
+    A.ps = A.us = nullptr;
+    // superposition backwards, interface transposed, moments
+    {
+        Phase ph(h, 3);
+        CUDA_TRY(h, launch_adj_assemble2d(h->P, A, nitems, h->ncell_i_max, st));
+        h->launches[3] += 1;
+    }
+    if (h->nif > 0) {
+        if ((rc = solve_interface_T(h))) return rc;
+        Phase ph(h, 3);
+        CUDA_TRY(h, launch_adj_moments(h->P, h->mth, A, nitems, st));
+        h->launches[3] += 1;
+    }
+    // basis and particular problems backwards
+    {
+        Phase ph(h, 0);
+        for (auto& cl : W.classes) {
+            CUDA_TRY(h, launch_adj_local2d(h->P, h->mth, A, W.jobs + cl.off, cl.count, cl.bw, cl.nw, cl.smem, st));
+            h->launches[0] += 1;
+        }
+    }
+    long long maxc = 0;
+    for (auto& md : h->mem) maxc = std::max(maxc, (long long)md.n[0] * md.n[1] * md.n[2]);
+    double* out = device_ptrs ? g_logK : W.gout;
+    CUDA_TRY(h, launch_grad_logK(h->d_mem, (int)h->mem.size(), maxc, h->d_K, h->d_Tf, h->d_hk, A, out, st));
+    if (!device_ptrs)
+        CUDA_TRY(h, cudaMemcpyAsync(g_logK, W.gout, sizeof(double) * cells, cudaMemcpyDeviceToHost, st));
+    return check_status(h);
 }
 
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl) {

@@ -1,0 +1,446 @@
+// Device building blocks of the 2D local solves, shared by the forward
+// kernels (local2d.cu) and their adjoints (adjoint2d.cu): the box and its
+// cell-centred RT0 operator (Sec. 2.2), the block LDL^T factorisation over
+// grid lines, warp-level solves (FP64, or FP32 sweeps with FP64 residual
+// refinement), right-hand-side generators and the bulk-copy helpers.
+#pragma once
+#include "mrcm_internal.cuh"
+#include <type_traits>
+
+namespace {
+
+constexpr int NWARP = 4;
+
+// 1/x in FP64: FP32 reciprocal refined by two Newton steps (error ~ u_64).
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
+}
+
+// Box description shared by all threads of a CTA.
+struct Box {
+    int lo[2], hi[2];
+    int nx, ny, n;
+    int kind[4];      // 0 Neumann, 1 Dirichlet, 2 Robin
+    double val[4];    // physical data (g or z)
+    double alpha;
+    double rlen[4];   // 1 / (faces on the side)
+};
+
+// side offsets into the per-side boundary arrays: x sides have ny faces,
+// y sides have nx faces.
+__device__ __forceinline__ int side_off(const Box& B, int sid) {
+    return sid == 0 ? 0 : sid == 1 ? B.ny : sid == 2 ? 2 * B.ny : 2 * B.ny + B.nx;
+}
+
+// P0: 1; P1: affine coordinate of the face centre along the side, in [-1, 1].
+__device__ __forceinline__ double psi_val(int m, int pos, int len, double rlen) {
+    return m == 0 ? 1.0 : (double)(2 * pos + 1 - len) * rlen;
+}
+
+// Shared-memory copy of the box operator.
+struct Ops {
+    double* cd;   // diagonal
+    double* cx;   // coupling of cell (i, j) with (i + 1, j)
+    double* cy;   // coupling of cell (i, j) with (i, j + 1)
+    double* hk;   // h / (2K) per cell, x and y interleaved [2n]
+    double* bT;   // boundary-face transmissibility per side
+    double* bB;   // Robin beta per side
+    double* dsc;  // Jacobi scale (1 in the FP64 form)
+};
+
+// Loads the face coefficients of the box and forms the boundary faces.
+__device__ void build_ops(const Box& B, const MemberDev& md, const DevPtrs& P, Ops& O) {
+    const double* Tf = P.Tf + md.cell_off * 3;
+    const double* hkg = P.hk + md.cell_off * 3;
+    const double* wh = P.wh + md.cell_off * 3;
+    const int nxg = md.n[0];
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
+        const int i = c % B.nx, j = c / B.nx;
+        const long long g = (B.lo[0] + i) + (long long)nxg * (B.lo[1] + j);
+        O.cx[c] = i < B.nx - 1 ? Tf[g * 3 + 0] : 0.0;
+        O.cy[c] = j < B.ny - 1 ? Tf[g * 3 + 1] : 0.0;
+        O.hk[2 * c] = hkg[g * 3 + 0];
+        O.hk[2 * c + 1] = hkg[g * 3 + 1];
+    }
+    const double ax = md.h[1], ay = md.h[0];  // face areas (normal to x, normal to y)
+    for (int sid = 0; sid < 4; ++sid) {
+        const int a = sid >> 1;
+        const int len = a == 0 ? B.ny : B.nx;
+        const double area = a == 0 ? ax : ay;
+        const int off = side_off(B, sid);
+        for (int pos = threadIdx.x; pos < len; pos += blockDim.x) {
+            int i, j;
+            if (a == 0) { j = pos; i = (sid == 0) ? 0 : B.nx - 1; }
+            else        { i = pos; j = (sid == 2) ? 0 : B.ny - 1; }
+            const long long g = (B.lo[0] + i) + (long long)nxg * (B.lo[1] + j);
+            const double hin = hkg[g * 3 + a];
+            double T = 0.0, beta = 0.0;
+            if (B.kind[sid] == 2) {
+                // the face to the outside cell: owned by the lower of the two cells
+                const long long gf = (sid & 1) ? g : g - (a == 0 ? 1 : nxg);
+                beta = B.alpha * wh[gf * 3 + a];
+                T = area * rcp64(hin + beta);
+            } else if (B.kind[sid] == 1) {
+                T = area * rcp64(hin);
+            }
+            O.bT[off + pos] = T;
+            O.bB[off + pos] = beta;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
+        const int i = c % B.nx, j = c / B.nx;
+        double d = O.cx[c] + O.cy[c];
+        if (i > 0) d += O.cx[c - 1];
+        if (j > 0) d += O.cy[c - B.nx];
+        if (i == 0) d += O.bT[side_off(B, 0) + j];
+        if (i == B.nx - 1) d += O.bT[side_off(B, 1) + j];
+        if (j == 0) d += O.bT[side_off(B, 2) + i];
+        if (j == B.ny - 1) d += O.bT[side_off(B, 3) + i];
+        O.cd[c] = d;
+    }
+    __syncthreads();
+}
+
+// (A x)_c for the unscaled FP64 operator.
+__device__ __forceinline__ double apply_A(const Box& B, const Ops& O, const double* x, int i, int j) {
+    const int c = j * B.nx + i;
+    double s = O.cd[c] * x[c];
+    if (i > 0) s -= O.cx[c - 1] * x[c - 1];
+    if (i < B.nx - 1) s -= O.cx[c] * x[c + 1];
+    if (j > 0) s -= O.cy[c - B.nx] * x[c - B.nx];
+    if (j < B.ny - 1) s -= O.cy[c] * x[c + B.nx];
+    return s;
+}
+
+// In-register Gauss-Jordan inverse of an SPD b x b block (row i in lane i).
+// Pivot reciprocals in FP64.  Writes Sout (row-major, b x b).
+template <typename T, int BW>
+__device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
+    const int lane = threadIdx.x & 31;
+    T a[BW];
+#pragma unroll
+    for (int c = 0; c < BW; ++c) a[c] = (lane < b && c < b) ? S[lane * b + c] : T(lane == c ? 1 : 0);
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+        if (k < b) {
+            if (lane == k) {
+#pragma unroll
+                for (int c = 0; c < BW; ++c) rowbuf[c] = a[c];
+            }
+            __syncwarp();
+            double piv = (double)rowbuf[k];
+            if (!(piv > 0.0)) {
+                if (lane == 0) *bad = 1;
+                piv = 1.0;
+            }
+            // FP32 form: __frcp_rn is the FP64 reciprocal rounded to FP32
+            const T ip = std::is_same<T, float>::value ? (T)__frcp_rn((float)piv) : (T)rcp64(piv);
+            if (lane == k) {
+#pragma unroll
+                for (int c = 0; c < BW; ++c) a[c] = (c == k) ? ip : a[c] * ip;
+            } else {
+                const T fip = a[k] * ip;
+#pragma unroll
+                for (int c = 0; c < BW; ++c) a[c] = (c == k) ? -fip : a[c] - fip * rowbuf[c];
+            }
+            __syncwarp();
+        }
+    }
+    if (lane < b) {
+#pragma unroll
+        for (int c = 0; c < BW; ++c)
+            if (c < b) Sout[lane * b + c] = a[c];
+    }
+    __syncwarp();
+}
+
+// Block LDL^T factorisation: Sinv[j] = S_j^{-1}.  cys = scaled line coupling
+// (type T).  All threads participate.
+template <typename T, int BW>
+__device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* Sbuf, T* rowbuf, int* bad) {
+    const int b = B.nx, nb = B.ny;
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+        cys[c] = (T)(O.cy[c] * O.dsc[c] * ((c + b < B.n) ? O.dsc[c + b] : 0.0));
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
+            const int i = t / b, k = t - (t / b) * b;
+            const int ci = j * b + i, ck = j * b + k;
+            if (i == k) {
+                double s = O.cd[ci] * O.dsc[ci] * O.dsc[ci];
+                if (j > 0) {
+                    const double cc = (double)cys[ci - b];
+                    s -= cc * cc * (double)Sinv[((j - 1) * b + i) * b + i];
+                }
+                Sbuf[t] = (T)s;
+            } else {
+                T s = T(0);
+                if (k == i + 1) s = (T)(-O.cx[ci] * O.dsc[ci] * O.dsc[ck]);
+                if (k == i - 1) s = (T)(-O.cx[ck] * O.dsc[ci] * O.dsc[ck]);
+                if (j > 0) s -= cys[ci - b] * Sinv[((j - 1) * b + i) * b + k] * cys[ck - b];
+                Sbuf[t] = s;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) gj_invert<T, BW>(Sbuf, Sinv + (size_t)j * b * b, b, rowbuf, bad);
+        __syncthreads();
+    }
+}
+
+// One warp sweeps in place: on entry w holds the scaled right-hand side, on
+// exit the scaled solution.
+template <typename T>
+__device__ void warp_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys, T* w, T* zbuf,
+                            int b, int nb) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < nb; ++j) {
+        if (lane < b) {
+            T z = w[j * b + lane];
+            if (j > 0) z += cys[(j - 1) * b + lane] * w[(j - 1) * b + lane];
+            zbuf[lane] = z;
+        }
+        __syncwarp();
+        if (lane < b) {
+            const T* S = Sinv + (size_t)j * b * b;
+            T acc0 = T(0), acc1 = T(0);
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                acc0 += S[k * b + lane] * zbuf[k];
+                acc1 += S[(k + 1) * b + lane] * zbuf[k + 1];
+            }
+            if (k < b) acc0 += S[k * b + lane] * zbuf[k];
+            w[j * b + lane] = acc0 + acc1;
+        }
+        __syncwarp();
+    }
+    for (int j = nb - 2; j >= 0; --j) {
+        if (lane < b) zbuf[lane] = cys[j * b + lane] * w[(j + 1) * b + lane];
+        __syncwarp();
+        if (lane < b) {
+            const T* S = Sinv + (size_t)j * b * b;
+            T acc0 = T(0), acc1 = T(0);
+            int k = 0;
+            for (; k + 1 < b; k += 2) {
+                acc0 += S[k * b + lane] * zbuf[k];
+                acc1 += S[(k + 1) * b + lane] * zbuf[k + 1];
+            }
+            if (k < b) acc0 += S[k * b + lane] * zbuf[k];
+            w[j * b + lane] += acc0 + acc1;
+        }
+        __syncwarp();
+    }
+}
+
+// Right-hand side generators -------------------------------------------------
+
+// Basis problem: Robin data psi_m on side sk of the box, homogeneous elsewhere.
+struct RhsBasis {
+    int sk, m;
+    __device__ double operator()(const Box& B, const Ops& O, int i, int j) const {
+        const int a = sk >> 1;
+        const bool on = (sk == 0 && i == 0) || (sk == 1 && i == B.nx - 1) || (sk == 2 && j == 0) ||
+                        (sk == 3 && j == B.ny - 1);
+        if (!on) return 0.0;
+        const int pos = a == 0 ? j : i;
+        const int len = a == 0 ? B.ny : B.nx;
+        return O.bT[side_off(B, sk) + pos] * psi_val(m, pos, len, B.rlen[sk]);
+    }
+};
+
+// Fixed right-hand side kept in shared memory (sources + boundary data).
+struct RhsStored {
+    const double* b;
+    __device__ double operator()(const Box& B, const Ops&, int i, int j) const { return b[j * B.nx + i]; }
+};
+
+// f |c| + Dirichlet / Neumann data + Robin data lam (lam may be null).
+__device__ double source_rhs(const Box& B, const Ops& O, const double* fm, int nxg, double vol, double ax,
+                             double ay, const double* lam, int i, int j) {
+    double r = fm[(B.lo[0] + i) + (long long)nxg * (B.lo[1] + j)] * vol;
+    const int sides[4] = {i == 0 ? 0 : -1, i == B.nx - 1 ? 1 : -1, j == 0 ? 2 : -1, j == B.ny - 1 ? 3 : -1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int sid = sides[q];
+        if (sid < 0) continue;
+        const int pos = (sid >> 1) == 0 ? j : i;
+        const double area = (sid >> 1) == 0 ? ax : ay;
+        if (B.kind[sid] == 1) r += O.bT[side_off(B, sid) + pos] * B.val[sid];
+        else if (B.kind[sid] == 0) r -= area * B.val[sid];
+        else if (lam) r += O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos];
+    }
+    return r;
+}
+
+// Solves A x = b for one right-hand side with one warp.  FP64 form: one
+// solve.  Mixed form: FP32 sweeps + FP64 residual refinement.  Returns the
+// number of sweeps (solves) performed.
+template <typename T, typename Rhs>
+__device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys, double* x, T* w,
+                          T* zbuf, const Rhs& rhs, double tol, int max_ir, int* noconv) {
+    const int lane = threadIdx.x & 31;
+    const int b = B.nx, nb = B.ny;
+    if (std::is_same<T, double>::value) {
+        for (int j = 0; j < nb; ++j)
+            for (int i = lane; i < b; i += 32) w[j * b + i] = (T)rhs(B, O, i, j);
+        __syncwarp();
+        warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
+        return 1;
+    } else {
+        float bn = 0.f;
+        for (int j = 0; j < nb; ++j)
+            for (int i = lane; i < b; i += 32) {
+                const int c = j * b + i;
+                const T wc = (T)(O.dsc[c] * rhs(B, O, i, j));
+                x[c] = 0.0;
+                w[c] = wc;
+                bn = fmaxf(bn, fabsf((float)wc));
+            }
+        for (int o = 16; o; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+        __syncwarp();
+        int it = 0;
+        for (; it < max_ir; ++it) {
+            warp_sweeps<T>(Sinv, cys, w, zbuf, b, nb);
+            for (int c = lane; c < B.n; c += 32) x[c] += O.dsc[c] * (double)w[c];
+            __syncwarp();
+            // FP64 residual of the unscaled operator; the (scaled) norms are taken in FP32
+            float rn = 0.f;
+            for (int j = 0; j < nb; ++j)
+                for (int i = lane; i < b; i += 32) {
+                    const int c = j * b + i;
+                    const T wc = (T)(O.dsc[c] * (rhs(B, O, i, j) - apply_A(B, O, x, i, j)));
+                    w[c] = wc;
+                    rn = fmaxf(rn, fabsf((float)wc));
+                }
+            for (int o = 16; o; o >>= 1) rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
+            __syncwarp();
+            if ((double)rn <= tol * (double)bn || bn == 0.f) { ++it; break; }
+            if (it == max_ir - 1 && lane == 0) *noconv = 1;
+        }
+        return it;
+    }
+}
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+// Shared-memory carve-up ----------------------------------------------------
+template <typename T>
+struct Carve {
+    Ops O;
+    T* Sinv;
+    T* cys;
+    T* Sbuf;
+    T* rowbuf;
+    T* zbuf;   // NWARP * 32
+    double* bsrc; // n: fixed right-hand side of the particular problem
+    double* X; // nrhs * n
+    T* W;      // nrhs * n
+    int* flags;
+};
+
+template <typename T>
+__host__ __device__ inline size_t carve_bytes(int nx, int ny, int nrhs) {
+    const size_t n = (size_t)nx * ny;
+    size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);  // cd cx cy dsc hk
+    s += align16(sizeof(double) * 2 * (nx + ny)) * 2;                                 // bT bB
+    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) + align16(sizeof(T) * nx * nx);
+    s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * NWARP) + align16(sizeof(double) * n);
+    if (std::is_same<T, float>::value) s += align16(sizeof(double) * n * nrhs);
+    s += align16(sizeof(T) * n * nrhs);
+    return s + 64;
+}
+
+template <typename T>
+__device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
+    Carve<T> C;
+    const size_t n = (size_t)nx * ny;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { unsigned char* p = base + o; o += align16(bytes); return p; };
+    C.O.cd = (double*)take(sizeof(double) * n);
+    C.O.cx = (double*)take(sizeof(double) * n);
+    C.O.cy = (double*)take(sizeof(double) * n);
+    C.O.dsc = (double*)take(sizeof(double) * n);
+    C.O.hk = (double*)take(sizeof(double) * 2 * n);
+    C.O.bT = (double*)take(sizeof(double) * 2 * (nx + ny));
+    C.O.bB = (double*)take(sizeof(double) * 2 * (nx + ny));
+    C.Sinv = (T*)take(sizeof(T) * n * nx);
+    C.cys = (T*)take(sizeof(T) * n);
+    C.Sbuf = (T*)take(sizeof(T) * nx * nx);
+    C.rowbuf = (T*)take(sizeof(T) * 32);
+    C.zbuf = (T*)take(sizeof(T) * 32 * NWARP);
+    C.bsrc = (double*)take(sizeof(double) * n);
+    if (std::is_same<T, float>::value) C.X = (double*)take(sizeof(double) * n * nrhs);
+    C.W = (T*)take(sizeof(T) * n * nrhs);
+    if (std::is_same<T, double>::value) C.X = (double*)C.W;
+    C.flags = (int*)take(64);
+    return C;
+}
+
+__device__ void setup_box(Box& B, const MemberDev& md, const int* lo, const int* hi, double alpha) {
+    for (int a = 0; a < 2; ++a) {
+        B.lo[a] = lo[a];
+        B.hi[a] = hi[a];
+    }
+    B.nx = hi[0] - lo[0];
+    B.ny = hi[1] - lo[1];
+    B.n = B.nx * B.ny;
+    B.alpha = alpha;
+    for (int sid = 0; sid < 4; ++sid) {
+        const int a = sid >> 1;
+        const bool phys = (sid & 1) ? (hi[a] == md.n[a]) : (lo[a] == 0);
+        if (phys) {
+            B.kind[sid] = md.bc_kind[sid] == 1 ? 1 : 0;
+            B.val[sid] = md.bc_val[sid];
+        } else {
+            B.kind[sid] = 2;
+            B.val[sid] = 0.0;
+        }
+        B.rlen[sid] = 1.0 / (double)(a == 0 ? B.ny : B.nx);
+    }
+}
+
+__device__ void fill_scale(const Box& B, Ops& O, bool mixed) {
+    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+        O.dsc[c] = mixed ? (double)rsqrtf((float)O.cd[c]) : 1.0;
+    __syncthreads();
+}
+
+// --- bulk (TMA engine) copy global -> shared with an mbarrier -------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Waits for phase `parity` of the barrier for at most ~2^31 cycles (about a
+// second); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
+
+}  // namespace

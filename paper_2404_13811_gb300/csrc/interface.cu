@@ -430,6 +430,157 @@ __global__ void k_if_update(IfPtrs I, int ncols) {
 }
 
 // ---------------------------------------------------------------------------
+// Transposed solve G^T y = z (the interface step of the adjoint).  The FP32
+// block-cyclic-reduction factors of R G C are applied transposed:
+//   (R G C)^-T = C^-1 ... : with M^-1 = B_0 ... B_{L-2} F_{L-1} ... F_0 the
+// forward sweep (F_l per level, then B_l back down), M^-T applies B_l^T for
+// l = 0 .. L-2 and then F_l^T for l = L-1 .. 0.  FP64 residuals of the
+// unscaled G^T drive the refinement as in the forward solve:
+//   r = z - G^T y,  bq = C r,  bq <- M^-T bq,  y += R bq.
+// ---------------------------------------------------------------------------
+
+// r = z - G^T y, gathered per column: the rows that reference column c are
+// the owner's own rows (first block) and its neighbours' rows whose second
+// block is the owner.
+__global__ void k_if_residualT(IfPtrs I, const SubDev* sub, const int* col_item, const double* z,
+                               const double* y, const int* row_member, int ncols, int first) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    const SubDev sd = sub[col_item[c]];
+    const int k = c - sd.col0;
+    const int NB = I.NB;
+    double s = z[c];
+    for (int q = 0; q < sd.nbasis; ++q) {
+        const int row = sd.col0 + q;
+        s -= I.Gv[(size_t)row * 2 * NB + k] * y[row];
+    }
+    for (int sid = 0; sid < MRCM_MAXSIDE; ++sid) {
+        const int t = sd.nbr[sid];
+        if (t < 0) continue;
+        const SubDev st = sub[t];
+        for (int q = 0; q < st.nbasis; ++q) {
+            const int row = st.col0 + q;
+            if (I.Gc[2 * row + 1] == sd.col0) s -= I.Gv[(size_t)row * 2 * NB + NB + k] * y[row];
+        }
+    }
+    I.r[c] = s;
+    I.bq[c] = (float)(I.Cs[c] * s);
+    const int m = row_member[c];
+    atomic_max_pos(&I.rnorm[2 * m], fabs(s));
+    if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(z[c]));
+}
+
+// B_l^T for the eliminations of one level: v_jm -= Cdn_j^T (Dinv_j[:, vrows]^T v_j)
+// (up = 0) or v_jp -= Cup_j^T (Dinv_j[:, mrows]^T v_j) (up = 1).  Each
+// surviving slab receives from one elimination per launch.
+__global__ void __launch_bounds__(256) k_bcr_bwdT(IfPtrs I, const ElimDev* el, int nel, int up) {
+    extern __shared__ float tsm[];
+    const int e = blockIdx.x;
+    if (e >= nel) return;
+    const ElimDev E = el[e];
+    if (up && E.jp < 0) return;
+    const SlabDev Sj = I.slabs[E.j];
+    const int np = I.npad;
+    const float* Dinv = I.Dinv + Sj.offD;
+    const int* rows = I.idx + Sj.offIdx + (up ? 0 : Sj.nm);
+    const int nq = up ? Sj.nm : Sj.nv;
+    float* vj = tsm;
+    float* t = tsm + np;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) vj[r] = I.bq[Sj.col0 + r];
+    __syncthreads();
+    for (int q = warp; q < nq; q += nwarp) {
+        const float acc = warp_dot(Dinv + (size_t)rows[q] * np, vj, Sj.n);
+        if ((threadIdx.x & 31) == 0) t[q] = acc;
+    }
+    __syncthreads();
+    const SlabDev St = I.slabs[up ? E.jp : E.jm];
+    const float* Cq = I.Cup + (up ? Sj.offCup : Sj.offCdn);
+    float* bt = I.bq + St.col0;
+    for (int c = threadIdx.x; c < St.n; c += blockDim.x) {
+        float acc = 0.f;
+        for (int q = 0; q < nq; ++q) acc += Cq[(size_t)q * Sj.ldc + c] * t[q];
+        bt[c] -= acc;
+    }
+}
+
+// F_l^T for the eliminations of one level:
+// b_j -= Rup^T b_jm[mrows_jm] + Rdn^T b_jp[vrows_jp], then b_j <- Dinv_j^T b_j.
+__global__ void __launch_bounds__(256) k_bcr_fwdT(IfPtrs I, const ElimDev* el, int nel) {
+    extern __shared__ float fts[];
+    const int e = blockIdx.x;
+    if (e >= nel) return;
+    const ElimDev E = el[e];
+    const SlabDev Sj = I.slabs[E.j];
+    const int np = I.npad;
+    float* bs = fts;          // n_j
+    float* gv = fts + np;     // neighbour rows
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bs[r] = I.bq[Sj.col0 + r];
+    if (E.jm >= 0 && E.jm != E.j) {
+        const SlabDev Sm = I.slabs[E.jm];
+        const int* mrows_m = I.idx + Sm.offIdx;
+        const float* Rup = I.Rup + Sj.offRup;   // nm_jm x n_j
+        __syncthreads();
+        for (int q = threadIdx.x; q < Sm.nm; q += blockDim.x) gv[q] = I.bq[Sm.col0 + mrows_m[q]];
+        __syncthreads();
+        for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
+            float acc = 0.f;
+            for (int q = 0; q < Sm.nm; ++q) acc += Rup[(size_t)q * Sj.n + r] * gv[q];
+            bs[r] -= acc;
+        }
+    }
+    if (E.jp >= 0) {
+        const SlabDev Sp = I.slabs[E.jp];
+        const int* vrows_p = I.idx + Sp.offIdx + Sp.nm;
+        const float* Rdn = I.Rdn + Sj.offRdn;   // nv_jp x n_j
+        __syncthreads();
+        for (int q = threadIdx.x; q < Sp.nv; q += blockDim.x) gv[q] = I.bq[Sp.col0 + vrows_p[q]];
+        __syncthreads();
+        for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
+            float acc = 0.f;
+            for (int q = 0; q < Sp.nv; ++q) acc += Rdn[(size_t)q * Sj.n + r] * gv[q];
+            bs[r] -= acc;
+        }
+    }
+    __syncthreads();
+    const float* Dinv = I.Dinv + Sj.offD;
+    for (int r = warp; r < Sj.n; r += nwarp) {
+        const float acc = warp_dot(Dinv + (size_t)r * np, bs, Sj.n);
+        if ((threadIdx.x & 31) == 0) I.bq[Sj.col0 + r] = acc;
+    }
+}
+
+__global__ void k_if_updateT(IfPtrs I, double* y, int nrows) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    y[r] += I.R[r] * (double)I.bq[r];
+}
+
+cudaError_t if_residualT(const IfPtrs& I, const SubDev* sub, const int* col_item, const double* z,
+                         const double* y, const int* row_member, int n, int first, cudaStream_t s) {
+    k_if_residualT<<<(n + 255) / 256, 256, 0, s>>>(I, sub, col_item, z, y, row_member, n, first);
+    return cudaGetLastError();
+}
+
+cudaError_t bcr_bwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, int up, cudaStream_t s) {
+    if (nel == 0) return cudaSuccess;
+    k_bcr_bwdT<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel, up);
+    return cudaGetLastError();
+}
+
+cudaError_t bcr_fwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
+    if (nel == 0) return cudaSuccess;
+    k_bcr_fwdT<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel);
+    return cudaGetLastError();
+}
+
+cudaError_t if_updateT(const IfPtrs& I, double* y, int n, cudaStream_t s) {
+    k_if_updateT<<<(n + 255) / 256, 256, 0, s>>>(I, y, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 cudaError_t if_assemble(const DevPtrs& P, const MethodDev& M, const IfPtrs& I, int nitems, int nrows,

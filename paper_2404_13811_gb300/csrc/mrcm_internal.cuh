@@ -125,10 +125,29 @@ struct IfPtrs {
     int npad;
 };
 
+// Device pointers of the reverse (adjoint) pass.  Seeds and results live in
+// the state layout; face-coefficient adjoints in the layout of Tf / hk / wh.
+struct AdjPtrs {
+    double* gp;          // [ncells]       dL/dp of the current state
+    double* gu;          // [ncells][2d]   dL/du
+    double* gTf;         // [ncells][3]    dL/dTf
+    double* ghk;         // [ncells][3]    dL/d(h / 2K)
+    double* gwh;         // [ncells][3]    dL/d(H / K_H)
+    const double* ps;    // state recorded before the colour pass being reversed
+    const double* us;
+    double* gps;         // [item][ncell_i_max]        dL/d(assembled Omega_i pressure)
+    double* gug;         // [item][6][side_max]        dL/d(Gamma_i face velocity)
+    double* gX;          // [nif]                      dL/dX
+    double* y;           // [nif]                      G^-T dL/dX  (= dL/drhs)
+    double* gmom;        // like DevPtrs::mom          dL/d(moments)
+    const double* X;     // forward interface solution
+};
+
 // status bits
 #define ST_NOT_SPD 1
 #define ST_NO_CONV 2
 #define ST_SINGULAR 4
 #define ST_BAD 8
+#define ST_BAD_K 16      // a permeability that is not positive and finite
 
 static inline __host__ __device__ int side_axis(int sid) { return sid >> 1; }

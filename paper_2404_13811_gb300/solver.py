@@ -65,12 +65,15 @@ class MRCM:
 
     def build_basis(self):
         L.mrcm_build_basis(self.h)
+        self._version = getattr(self, "_version", 0) + 1
 
     def solve_interface(self):
         L.mrcm_solve_interface(self.h)
+        self._version = getattr(self, "_version", 0) + 1
 
     def smooth(self, n_steps):
         L.mrcm_smooth(self.h, n_steps)
+        self._version = getattr(self, "_version", 0) + 1
 
     def fluxes(self, member=0, device=False):
         """(p [ncells], u [ncells, 2d]) of one member, x-fastest cell order."""
@@ -85,6 +88,49 @@ class MRCM:
             u = np.empty((nc, 2 * pr.dim))
         L.mrcm_fluxes(self.h, member, u, p)
         return p, u
+
+    @property
+    def ncells(self):
+        return int(sum(int(np.prod(pr.n)) for pr in self.problems))
+
+    def state(self):
+        """(p [total cells], u [total cells, 2d]) of all members, concatenated
+        in member order, as new CUDA tensors."""
+        import torch
+        nc = self.ncells
+        p = torch.empty(nc, dtype=torch.float64, device="cuda")
+        u = torch.empty((nc, 2 * self.dim), dtype=torch.float64, device="cuda")
+        off = 0
+        for m, pr in enumerate(self.problems):
+            k = int(np.prod(pr.n))
+            L.mrcm_fluxes(self.h, m, u[off:off + k], p[off:off + k])
+            off += k
+        return p, u
+
+    def set_permeability(self, values, log=False):
+        """New K (or log K with log=True) for every cell of every member,
+        concatenated in member order; numpy (host) or a CUDA tensor."""
+        if not hasattr(values, "data_ptr"):
+            values = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
+        L.mrcm_set_permeability(self.h, values, int(log))
+        self._version = getattr(self, "_version", 0) + 1
+
+    def adjoint(self, gp=None, gu=None):
+        """dL/dlog K [total cells] of a scalar L of the current solution, from
+        dL/dp [total cells] and dL/du [total cells, 2d] (either may be None).
+        CUDA tensors in, CUDA tensor out; numpy in, numpy out."""
+        dev = any(hasattr(a, "data_ptr") for a in (gp, gu) if a is not None)
+        if dev or (gp is None and gu is None):
+            import torch
+            out = torch.empty(self.ncells, dtype=torch.float64, device="cuda")
+            gp = gp.contiguous() if gp is not None else None
+            gu = gu.contiguous() if gu is not None else None
+        else:
+            out = np.empty(self.ncells)
+            gp = np.ascontiguousarray(gp, dtype=np.float64) if gp is not None else None
+            gu = np.ascontiguousarray(gu, dtype=np.float64) if gu is not None else None
+        L.mrcm_adjoint(self.h, gp, gu, out)
+        return out
 
     def stats(self):
         return L.mrcm_stats(self.h)
@@ -110,3 +156,47 @@ class MRCM:
         """One full step (basis, interface, n_smooth smoothing steps); graph=True
         replays it as one captured CUDA graph after the first (eager) call."""
         L.mrcm_run(self.h, n_smooth, int(graph))
+        self._version = getattr(self, "_version", 0) + 1
+
+
+def _autograd_function():
+    import torch
+
+    class MRCMSolve(torch.autograd.Function):
+        """(p, u) = MRCM-OS(log K) with the library's adjoint as backward.
+
+        forward: sets log K, runs one whole step with n_smooth smoothing
+        steps and returns the state of all members (concatenated).  backward:
+        one mrcm_adjoint call, which reuses the handle's kept factors.  The
+        backward must run before the handle solves again."""
+
+        @staticmethod
+        def forward(ctx, logK, solver, n_smooth):
+            solver.set_permeability(logK.detach().contiguous(), log=True)
+            solver.run(n_smooth)
+            ctx.solver = solver
+            ctx.version = solver._version
+            return solver.state()
+
+        @staticmethod
+        def backward(ctx, gp, gu):
+            solver = ctx.solver
+            if solver._version != ctx.version:
+                raise RuntimeError("the MRCM handle solved again after this forward; "
+                                   "run backward before the next forward on the same handle")
+            return solver.adjoint(gp, gu), None, None
+
+    return MRCMSolve
+
+
+_FN = None
+
+
+def mrcm_solve(solver, logK, n_smooth):
+    """Differentiable MRCM-OS: returns (p, u) of all members for the CUDA
+    tensor logK [total cells]; gradients with respect to logK come from the
+    hand-written adjoint (mrcm_adjoint)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(logK, solver, n_smooth)

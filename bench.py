@@ -163,7 +163,7 @@ def run_gpu(args, rank, world):
 
     def make(precision, device_inputs=True, tol=1e-12):
         return MRCM(prob, part, space=pm.space, alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth,
-                    precision=precision, ir_tol=tol, max_ir=8, stream=stream, device_inputs=device_inputs)
+                    precision=precision, ir_tol=tol, max_ir=30, stream=stream, device_inputs=device_inputs)
 
     def step(s):
         s.build_basis()

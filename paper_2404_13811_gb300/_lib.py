@@ -112,7 +112,7 @@ def make_structs(dim, n, h, bc_kind, bc_value, sub, overlap):
     return g, b, p
 
 
-def make_params(space, alpha_basis, alpha_smooth, precision, ir_tol=1e-12, max_ir=8):
+def make_params(space, alpha_basis, alpha_smooth, precision, ir_tol=1e-12, max_ir=30):
     q = mrcm_params()
     q.space = int(space)
     q.alpha_basis = float(alpha_basis)

@@ -41,7 +41,16 @@ cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
-size_t elim_smem_bytes(int nmv, int nmax);
+size_t elim_smem_bytes(int nmv, int cw);
+size_t lu_smem(int np, int xch);
+size_t local3d_smem(int prec, int nx, int ny, int nz, bool part);
+size_t smooth3d_smem(int prec, int nx, int ny, int nz);
+size_t factor3_entries(int nx, int ny, int nz);
+cudaError_t launch_local3d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_smooth3d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_assemble3d(const DevPtrs& P, const double* X, int nitems, int ncell_i_max, cudaStream_t s);
 cudaError_t if_residualT(const IfPtrs& I, const SubDev* sub, const int* col_item, const double* z,
                          const double* y, const int* row_member, int n, int first, cudaStream_t s);
 cudaError_t bcr_bwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, int up, cudaStream_t s);
@@ -125,6 +134,8 @@ struct mrcm_handle {
     double *d_K = nullptr, *d_f = nullptr, *d_p = nullptr, *d_u = nullptr;
     double *d_Tf = nullptr, *d_hk = nullptr, *d_wh = nullptr;
     void* d_fac = nullptr;
+    void* d_fac_aux = nullptr;
+    void* d_fac_part = nullptr;
     double* d_dsc = nullptr;
     double *d_Psi = nullptr, *d_Ug = nullptr, *d_pbar = nullptr, *d_ubg = nullptr, *d_mom = nullptr;
     int* d_status = nullptr;
@@ -390,7 +401,6 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         if (rc) return rc;
         if (grids[m].dim != h->dim) return fail(h, MRCM_ERR_BAD_INPUT, "members must share dim");
     }
-    if (h->dim != 2) return fail(h, MRCM_ERR_UNSUPPORTED, "3D subdomains are not available in this build");
     int rc = plan(h, grids, bcs, parts);
     if (rc) return rc;
     for (int m = 0; m < count; ++m) {
@@ -418,12 +428,26 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     // jobs: basis, particular, smoothing factor
     std::map<int, std::vector<Job>> byw;
     std::map<int, size_t> smem_w;
-    size_t fac_stride = 0, dsc_stride = 0;
+    size_t fac_stride = 0, dsc_stride = 0, part_stride = 0;
     const int nitems = (int)h->sub.size();
     for (int s = 0; s < nitems; ++s) {
         const SubDev& sd = h->sub[s];
-        int bx = sd.hih[0] - sd.loh[0], by = sd.hih[1] - sd.loh[1];
-        int ix = sd.hi[0] - sd.lo[0], iy = sd.hi[1] - sd.lo[1];
+        int bx = sd.hih[0] - sd.loh[0], by = sd.hih[1] - sd.loh[1], bz = sd.hih[2] - sd.loh[2];
+        int ix = sd.hi[0] - sd.lo[0], iy = sd.hi[1] - sd.lo[1], iz = sd.hi[2] - sd.lo[2];
+        if (d == 3) {
+            // one class; boxes are factored plane by plane with the factor in global memory
+            const int pb = bx * by * bz / std::max({bx, by, bz});
+            if (pb > 256) return fail(h, MRCM_ERR_UNSUPPORTED, "3D boxes with planes of more than 256 cells");
+            fac_stride = std::max(fac_stride, (factor3_entries(bx, by, bz) + 3) & ~size_t(3));
+            part_stride = std::max(part_stride, (factor3_entries(ix, iy, iz) + 3) & ~size_t(3));
+            dsc_stride = std::max(dsc_stride, (size_t)bx * by * bz);
+            byw[0].push_back(Job{s, JOB_BASIS});
+            byw[0].push_back(Job{s, JOB_PART});
+            if (!h->mth.same_alpha) byw[0].push_back(Job{s, JOB_SFACT});
+            smem_w[0] = std::max({smem_w[0], local3d_smem(prec, bx, by, bz, false), local3d_smem(prec, ix, iy, iz, true)});
+            h->smooth_smem = std::max(h->smooth_smem, smooth3d_smem(prec, bx, by, bz));
+            continue;
+        }
         if (bx > 32 || ix > 32)
             return fail(h, MRCM_ERR_UNSUPPORTED, "2D boxes wider than 32 cells along x are not supported");
         fac_stride = std::max(fac_stride, ((size_t)bx * bx * by + 3) & ~size_t(3));  // 16-byte aligned slots
@@ -438,6 +462,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         if (!h->mth.same_alpha) add(JOB_SFACT, bx, by, 0);
         h->smooth_smem = std::max(h->smooth_smem, smooth2d_smem(prec, bx, by));
     }
+    if (h->smooth_smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "subdomain box too large for shared memory");
     std::vector<Job> jobs;
     for (auto& kv : byw) {
         JobClass jc{kv.first, smem_w[kv.first], (int)jobs.size(), (int)kv.second.size()};
@@ -470,6 +495,14 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     if ((e = dalloc(h, &h->d_hk, h->ncells * 3))) return e;
     if ((e = dalloc(h, &h->d_wh, h->ncells * 3))) return e;
     if ((e = dalloc(h, (char**)&h->d_fac, fac_stride * nitems * tsz))) return e;
+    double* d_xs = nullptr;
+    if (d == 3) {
+        if ((e = dalloc(h, (char**)&h->d_fac_part, part_stride * nitems * tsz))) return e;
+        if (!h->mth.same_alpha && (e = dalloc(h, (char**)&h->d_fac_aux, fac_stride * nitems * tsz))) return e;
+        // FP64 iterates of the local solves: one slot of 4 right-hand sides per CTA of the largest launch
+        const size_t slots = std::max(jobs.size(), (size_t)nitems);
+        if ((e = dalloc(h, &d_xs, slots * 4 * dsc_stride))) return e;
+    }
     if ((e = dalloc(h, &h->d_dsc, dsc_stride * nitems))) return e;
     if ((e = dalloc(h, &h->d_Psi, (size_t)nitems * h->nbasis_max * h->ncell_i_max))) return e;
     if ((e = dalloc(h, &h->d_Ug, (size_t)nitems * h->nbasis_max * MRCM_MAXSIDE * h->side_max))) return e;
@@ -514,6 +547,11 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     P.u = h->d_u;
     P.fac = h->d_fac;
     P.fac_stride = (long long)fac_stride;
+    P.fac_aux = h->d_fac_aux;
+    P.fac_part = h->d_fac_part;
+    P.part_stride = (long long)part_stride;
+    P.xs = d_xs;
+    P.xs_stride = (long long)(4 * dsc_stride);
     P.dsc = h->d_dsc;
     P.dsc_stride = (long long)dsc_stride;
     P.Psi = h->d_Psi;
@@ -571,12 +609,17 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         offR += 2LL * sl.ldc * sl.n;
         sl.offPiv = (long long)j * npad;
     }
-    // Schur-update scratch: bounded by the largest couplings
+    // Schur-update scratch: bounded by the largest couplings; the coupling
+    // columns are staged in chunks that fit shared memory
+    int elim_cw = npad, xch = 64;
     {
         size_t nmv = 0;
         for (auto& sl : h->slabs) nmv = std::max(nmv, (size_t)std::max(sl.nm, sl.nv));
-        h->elim_smem = elim_smem_bytes((int)nmv, npad);
+        while (elim_cw > 32 && elim_smem_bytes((int)nmv, elim_cw) > 227 * 1024) elim_cw = (elim_cw + 1) / 2;
+        h->elim_smem = elim_smem_bytes((int)nmv, elim_cw);
         if (h->elim_smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface coupling blocks too large");
+        while (xch > 4 && lu_smem(npad, xch) > 227 * 1024) xch /= 2;
+        if (lu_smem(npad, xch) > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface slabs too large");
     }
     // elimination levels over all members
     int maxS = 0;
@@ -605,6 +648,8 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     const int NB = h->nbasis_max;
     I.NB = NB;
     I.npad = npad;
+    I.xch = xch;
+    I.elim_cw = elim_cw;
     if ((e = dalloc(h, &I.Gv, (size_t)h->nif * 2 * NB))) return e;
     if ((e = dalloc(h, &I.Gc, (size_t)h->nif * 2))) return e;
     if ((e = dalloc(h, &I.Gn, (size_t)h->nif * 2))) return e;
@@ -672,7 +717,9 @@ int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg) { return fail(
 static int issue_basis(mrcm_handle* h) {
     Phase ph(h, 0);
     for (auto& jc : h->jclasses) {
-        cudaError_t e = launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, h->stream);
+        cudaError_t e = h->dim == 3
+                            ? launch_local3d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.smem, h->stream)
+                            : launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, h->stream);
         if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
         h->launches[0] += 1;
     }
@@ -745,7 +792,8 @@ static int read_if_residual(mrcm_handle* h, double* worst) {
 
 static int issue_assemble(mrcm_handle* h) {
     Phase ph(h, 3);
-    CUDA_TRY(h, launch_assemble2d(h->P, h->I.x, (int)h->sub.size(), h->ncell_i_max, h->stream));
+    CUDA_TRY(h, h->dim == 3 ? launch_assemble3d(h->P, h->I.x, (int)h->sub.size(), h->ncell_i_max, h->stream)
+                            : launch_assemble2d(h->P, h->I.x, (int)h->sub.size(), h->ncell_i_max, h->stream));
     h->launches[3] += 1;
     return 0;
 }
@@ -756,7 +804,9 @@ static int issue_smooth(mrcm_handle* h, int n_steps) {
     for (int k = 0; k < n_steps; ++k) {
         for (int c = 0; c < nc; ++c) {
             const int off = h->colour_off[c], cnt = h->colour_off[c + 1] - off;
-            cudaError_t e = launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
+            cudaError_t e = h->dim == 3
+                                ? launch_smooth3d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream)
+                                : launch_smooth2d(h->P, h->mth, h->d_colour_items + off, cnt, h->smooth_smem, h->stream);
             if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("smoothing kernel: ") + cudaGetErrorString(e));
             h->launches[4] += 1;
         }
@@ -1107,6 +1157,7 @@ int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_l
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_adjoint needs a solution");
+    if (h->dim != 2) return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint is available for 2D problems");
     for (auto& md : h->mem)
         if (md.pure_neumann)
             return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint needs Dirichlet data on some side of every member");

@@ -22,7 +22,8 @@ constexpr int GJ_THREADS = 512;
 #define MRCM_PANEL_WARPS 8
 #endif
 constexpr int PANEL_WARPS = MRCM_PANEL_WARPS;   // warps that factor a panel
-constexpr int XCH = 64;          // inverse columns solved together in phase 2
+// inverse columns solved together in phase 2: IfPtrs::xch (64 unless the
+// slab is too large for shared memory)
 
 
 
@@ -195,19 +196,24 @@ __device__ void rows_times_cols(const float* L, int M, int K, const float* Dinv,
 // with C row-major (ld ldc) in global memory staged in shared memory.
 template <bool ACCUM_INTO_D>
 __device__ void apply_coupling(const float* Asm, int M, int M2, const float* Cg, int ldc, int ncol, float* Csm,
-                               float* D, int np, const int* rows, float* Cout, int ldout, int nclear) {
+                               int cwmax, float* D, int np, const int* rows, float* Cout, int ldout, int nclear) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < M2 * ncol; t += nt) {
-        const int q = t / ncol, c = t - (t / ncol) * ncol;
-        Csm[t] = Cg[(size_t)q * ldc + c];
-    }
-    __syncthreads();
-    for (int t = tid; t < M * ncol; t += nt) {
-        const int r = t / ncol, c = t - (t / ncol) * ncol;
-        float acc = 0.f;
-        for (int q = 0; q < M2; ++q) acc += Asm[r * M2 + q] * Csm[q * ncol + c];
-        if (ACCUM_INTO_D) D[(size_t)c * np + rows[r]] -= acc;
-        else Cout[(size_t)r * ldout + c] = -acc;
+    // columns in chunks of at most cwmax (the staged block is M2 x cw)
+    for (int c0 = 0; c0 < ncol; c0 += cwmax) {
+        const int cw = min(cwmax, ncol - c0);
+        __syncthreads();
+        for (int t = tid; t < M2 * cw; t += nt) {
+            const int q = t / cw, c = t - (t / cw) * cw;
+            Csm[t] = Cg[(size_t)q * ldc + c0 + c];
+        }
+        __syncthreads();
+        for (int t = tid; t < M * cw; t += nt) {
+            const int r = t / cw, c = t - (t / cw) * cw;
+            float acc = 0.f;
+            for (int q = 0; q < M2; ++q) acc += Asm[r * M2 + q] * Csm[q * cw + c];
+            if (ACCUM_INTO_D) D[(size_t)(c0 + c) * np + rows[r]] -= acc;
+            else Cout[(size_t)r * ldout + c0 + c] = -acc;
+        }
     }
     if (!ACCUM_INTO_D)
         for (int t = tid; t < M * (nclear - ncol); t += nt) {
@@ -286,16 +292,17 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
     __syncthreads();
     rows_times_cols(Lrows, M, Sj.n, Dinv, np, cols, N, Asm, stL, stQ);
     if (rank == 0) {
-        apply_coupling<true>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.D + Sm.offD, np, I.idx + Sm.offIdx, nullptr, 0, 0);
-    } else if (rank == 1) {
-        apply_coupling<false>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, nullptr, np, nullptr, I.Cup + Sm.offCup, Sm.ldc,
-                              Sm.ldc);
-    } else if (rank == 2) {
-        apply_coupling<true>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.D + Sp.offD, np, I.idx + Sp.offIdx + Sp.nm,
+        apply_coupling<true>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, I.D + Sm.offD, np, I.idx + Sm.offIdx,
                              nullptr, 0, 0);
+    } else if (rank == 1) {
+        apply_coupling<false>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.elim_cw, nullptr, np, nullptr, I.Cup + Sm.offCup,
+                              Sm.ldc, Sm.ldc);
+    } else if (rank == 2) {
+        apply_coupling<true>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.elim_cw, I.D + Sp.offD, np,
+                             I.idx + Sp.offIdx + Sp.nm, nullptr, 0, 0);
     } else {
-        apply_coupling<false>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, nullptr, np, nullptr, I.Cdn + Sp.offCdn, Sp.ldc,
-                              Sp.ldc);
+        apply_coupling<false>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, nullptr, np, nullptr, I.Cdn + Sp.offCdn,
+                              Sp.ldc, Sp.ldc);
     }
 }
 
@@ -678,6 +685,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     extern __shared__ __align__(16) float lsm[];
     float* Ps = lsm;                           // [c][r], GJ_NB * np
     float* Xs = Ps + GJ_NB * np;                          // phase 1 [c][jj] (ld ncmax), phase 2 [jj][r]
+    const int XCH = I.xch;
     float* Upy = Xs + max(GJ_NB * ncmax, XCH * np);       // [c][jj], max(GJ_NB * ncmax, np)
     int* piv = (int*)(Upy + max(GJ_NB * ncmax, np));  // np
     int* ownc = piv + np;                      // ncmax
@@ -929,11 +937,11 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     if (singular && tid == 0) atomicOr(status, ST_SINGULAR);
 }
 
-size_t lu_smem(int np) {
+size_t lu_smem(int np, int xch) {
     const int npan = (np + GJ_NB - 1) / GJ_NB;
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
-    const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)XCH * np);
+    const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)xch * np);
     return sizeof(float) * ((size_t)GJ_NB * np + xs + up) +
            sizeof(int) * ((size_t)np + ncmax + np) + 16;
 }
@@ -958,7 +966,7 @@ static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, si
 
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    const size_t smem = lu_smem(I.npad);
+    const size_t smem = lu_smem(I.npad, I.xch);
     static size_t set_smem = 0;
     if (smem > set_smem) {
         cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -970,9 +978,9 @@ cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status,
     return launch_cluster((const void*)k_lu_inverse, nel * GJ_CL, GJ_THREADS, smem, s, args);
 }
 
-size_t elim_smem_bytes(int nmv, int nmax) {
-    // Asm (nmv^2) + stL (nmv*32) + stQ (32*nmv) + Csm (nmv * nmax)
-    return sizeof(float) * ((size_t)nmv * nmv + 64 * (size_t)nmv + (size_t)nmv * nmax) + 16;
+size_t elim_smem_bytes(int nmv, int cw) {
+    // Asm (nmv^2) + stL (nmv*32) + stQ (32*nmv) + Csm (nmv * cw)
+    return sizeof(float) * ((size_t)nmv * nmv + 64 * (size_t)nmv + (size_t)nmv * cw) + 16;
 }
 
 cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s) {

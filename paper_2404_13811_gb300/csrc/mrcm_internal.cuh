@@ -79,6 +79,11 @@ struct DevPtrs {
     // factors kept for smoothing
     void* fac;           // T elements
     long long fac_stride;
+    void* fac_aux;       // 3D: factor of the basis box when alpha_basis != alpha_smooth
+    void* fac_part;      // 3D: factor of the Omega_i box of the particular problem
+    long long part_stride;
+    double* xs;          // 3D mixed form: FP64 iterates of the local solves, per CTA slot
+    long long xs_stride;
     double* dsc;         // Jacobi scaling of the smoothing operator (mixed form)
     long long dsc_stride;
     // basis data
@@ -123,6 +128,8 @@ struct IfPtrs {
     unsigned long long* rnorm;   // [2 * nmember]: residual max, rhs max (bit patterns)
     int NB;
     int npad;
+    int xch;       // inverse columns solved together by the slab LU (fits shared memory)
+    int elim_cw;   // coupling columns staged together by the Schur update
 };
 
 // Device pointers of the reverse (adjoint) pass.  Seeds and results live in

@@ -26,7 +26,7 @@ class MRCM:
     host) or CUDA tensors (copied on the device)."""
 
     def __init__(self, problems, partitions, space=1, alpha_basis=1.0, alpha_smooth=1.0,
-                 precision="fp64", ir_tol=1e-12, max_ir=8, stream=None, device_inputs=False):
+                 precision="fp64", ir_tol=1e-12, max_ir=30, stream=None, device_inputs=False):
         import torch
         single = not isinstance(problems, (list, tuple))
         self.problems = [problems] if single else list(problems)

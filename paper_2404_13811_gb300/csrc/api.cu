@@ -46,6 +46,7 @@ size_t lu_smem(int np, int xch);
 size_t local3d_smem(int prec, int nx, int ny, int nz, bool part);
 size_t smooth3d_smem(int prec, int nx, int ny, int nz);
 size_t factor3_entries(int nx, int ny, int nz);
+bool stage3_aligned(int prec, int nx, int ny, int nz);
 cudaError_t launch_local3d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, size_t smem,
                            cudaStream_t s);
 cudaError_t launch_smooth3d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,
@@ -438,6 +439,8 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
             // one class; boxes are factored plane by plane with the factor in global memory
             const int pb = bx * by * bz / std::max({bx, by, bz});
             if (pb > 256) return fail(h, MRCM_ERR_UNSUPPORTED, "3D boxes with planes of more than 256 cells");
+            if (!stage3_aligned(prec, bx, by, bz) || !stage3_aligned(prec, ix, iy, iz))
+                return fail(h, MRCM_ERR_UNSUPPORTED, "3D box layout breaks the 16-byte rule of the bulk copies");
             fac_stride = std::max(fac_stride, (factor3_entries(bx, by, bz) + 3) & ~size_t(3));
             part_stride = std::max(part_stride, (factor3_entries(ix, iy, iz) + 3) & ~size_t(3));
             dsc_stride = std::max(dsc_stride, (size_t)bx * by * bz);

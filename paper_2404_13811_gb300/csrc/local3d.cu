@@ -217,41 +217,73 @@ __device__ __forceinline__ double applyA3g(const Box3& B, const MemberDev& md, c
     return s;
 }
 
-// In-place Gauss-Jordan inverse of an SPD b x b matrix in shared memory by
-// the whole CTA (row-major).  Pivot reciprocals from the FP64 pivot.
+// 16-byte vectors of the shared-memory kernels (float4 / double2)
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <> struct V16<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
 template <typename T>
-__device__ void gj_cta(T* S, int b, T* rowbuf, T* colbuf, T* ipb, int* bad) {
+union VU {
+    typename V16<T>::V v;
+    T a[V16<T>::W];
+};
+
+// leading dimension of the shared plane block: b padded to 4 entries
+__host__ __device__ __forceinline__ int plane_ld(int b) { return (b + 3) & ~3; }
+
+// In-place Gauss-Jordan inverse of an SPD b x b matrix in shared memory by
+// the whole CTA (row-major, leading dimension ld = plane_ld(b), padding
+// columns zero).  Each thread updates 16-byte groups of a row.  Pivot
+// reciprocals from the FP64 pivot.
+template <typename T>
+__device__ void gj_cta(T* S, int b, int ld, T* rowbuf, T* colbuf, T* ipb, int* bad) {
+    constexpr int W = V16<T>::W;
+    using V = typename V16<T>::V;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int bb = b * b;
-    const int i0 = tid / b, c0 = tid - i0 * b;
-    const int di = nt / b, dc = nt - di * b;
+    const int ng = ld / W;                 // groups per row
+    const int tot = b * ng;
+    const int i0 = tid / ng, g0 = tid - i0 * ng;
+    const int di = nt / ng, dg = nt - di * ng;
     for (int k = 0; k < b; ++k) {
         if (tid == 0) {
-            double piv = (double)S[k * b + k];
+            double piv = (double)S[k * ld + k];
             if (!(piv > 0.0)) {
                 *bad = 1;
                 piv = 1.0;
             }
             *ipb = std::is_same<T, float>::value ? (T)__frcp_rn((float)piv) : (T)rcp64(piv);
         }
-        for (int t = tid; t < b; t += nt) {
-            colbuf[t] = S[t * b + k];
-            rowbuf[t] = S[k * b + t];
+        for (int t = tid; t < ld; t += nt) {
+            rowbuf[t] = S[k * ld + t];
+            if (t < b) colbuf[t] = S[t * ld + k];
         }
         __syncthreads();
         const T ip = *ipb;
-        int i = i0, c = c0;
-        for (int t = tid; t < bb; t += nt) {
+        const int gk = k / W, ek = k - gk * W;
+        int i = i0, g = g0;
+        for (int t = tid; t < tot; t += nt) {
+            VU<T> x, r;
+            x.v = *reinterpret_cast<const V*>(&S[i * ld + g * W]);
+            r.v = *reinterpret_cast<const V*>(&rowbuf[g * W]);
+            const bool colk = g == gk;
             if (i == k) {
-                S[t] = (c == k) ? ip : rowbuf[c] * ip;
+#pragma unroll
+                for (int e = 0; e < W; ++e) x.a[e] = (colk && e == ek) ? ip : r.a[e] * ip;
             } else {
                 const T f = colbuf[i] * ip;
-                S[t] = (c == k) ? -f : S[t] - f * rowbuf[c];
+#pragma unroll
+                for (int e = 0; e < W; ++e) x.a[e] = (colk && e == ek) ? -f : x.a[e] - f * r.a[e];
             }
-            c += dc;
+            *reinterpret_cast<V*>(&S[i * ld + g * W]) = x.v;
+            g += dg;
             i += di;
-            if (c >= b) {
-                c -= b;
+            if (g >= ng) {
+                g -= ng;
                 ++i;
             }
         }
@@ -259,27 +291,31 @@ __device__ void gj_cta(T* S, int b, T* rowbuf, T* colbuf, T* ipb, int* bad) {
     }
 }
 
-// Block LDL^T over planes; inverses of the plane Schur complements to F.
+// Block LDL^T over planes; inverses of the plane Schur complements to F
+// (row stride b, plane stride plane_stride(b)).  Sb: ld = plane_ld(b).
 template <typename T>
 __device__ void factor3(const Box3& B, const Ops3& O, const T* c2s, T* F, T* Sb, T* rowbuf, T* colbuf, T* ipb,
                         int* bad, bool mixed) {
-    const int b = B.b, bb = b * b;
+    const int b = B.b, ld = plane_ld(b), bb = b * b;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int i0 = tid / b, k0 = tid - i0 * b;
     const int di = nt / b, dk = nt - di * b;
     const int n0 = B.n[B.a0];
+    for (int t = tid; t < b * ld; t += nt) Sb[t] = T(0);   // padding columns stay zero
+    __syncthreads();
     for (int j = 0; j < B.np; ++j) {
         int i = i0, k = k0;
         for (int t = tid; t < bb; t += nt) {
             const int ci = j * b + i, ck = j * b + k;
+            const int sidx = i * ld + k;
             const double si = mixed ? O.dsc[ci] : 1.0;
             if (i == k) {
                 double s = O.cd[ci] * si * si;
                 if (j > 0) {
                     const double cc = (double)c2s[ci - b];
-                    s -= cc * cc * (double)Sb[t];
+                    s -= cc * cc * (double)Sb[sidx];
                 }
-                Sb[t] = (T)s;
+                Sb[sidx] = (T)s;
             } else {
                 const double sk = mixed ? O.dsc[ck] : 1.0;
                 T s = T(0);
@@ -287,8 +323,8 @@ __device__ void factor3(const Box3& B, const Ops3& O, const T* c2s, T* F, T* Sb,
                 else if (k == i - 1 && (O.nb[ci] & 1)) s = (T)(-O.c0[ck] * si * sk);
                 else if (k == i + n0) s = (T)(-O.c1[ci] * si * sk);
                 else if (k == i - n0) s = (T)(-O.c1[ck] * si * sk);
-                if (j > 0) s -= c2s[ci - b] * Sb[t] * c2s[ck - b];
-                Sb[t] = s;
+                if (j > 0) s -= c2s[ci - b] * Sb[sidx] * c2s[ck - b];
+                Sb[sidx] = s;
             }
             k += dk;
             i += di;
@@ -298,9 +334,20 @@ __device__ void factor3(const Box3& B, const Ops3& O, const T* c2s, T* F, T* Sb,
             }
         }
         __syncthreads();
-        gj_cta<T>(Sb, b, rowbuf, colbuf, ipb, bad);
+        gj_cta<T>(Sb, b, ld, rowbuf, colbuf, ipb, bad);
         T* Fj = F + (size_t)j * plane_stride(b);
-        for (int t = tid; t < bb; t += nt) Fj[t] = Sb[t];
+        {
+            int ii = i0, kk = k0;
+            for (int t = tid; t < bb; t += nt) {
+                Fj[t] = Sb[ii * ld + kk];
+                kk += dk;
+                ii += di;
+                if (kk >= b) {
+                    kk -= b;
+                    ++ii;
+                }
+            }
+        }
         // the solves read the factor through the bulk-copy (async) proxy
         asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();
@@ -312,12 +359,15 @@ __device__ void factor3(const Box3& B, const Ops3& O, const T* c2s, T* F, T* Sb,
 // solutions.  The plane inverses (symmetric, row-major, plane stride padded
 // to 16 bytes) stream from global memory through the bulk-copy (TMA) engine
 // in chunks of B.crows rows into two shared buffers: chunk s + 1 is in flight
-// while chunk s is used.  Thread (r, half) accumulates rows r, r + T3/2, ..
-// for the right-hand sides of its half.  Returns false when a copy did not
-// complete in time (the CTA then stops using the buffers).
+// while chunk s is used.  The sweep input of a plane is kept interleaved
+// (vb[c][4], all right-hand sides of a column in one 16-byte load).  For
+// b <= T3/2 the two halves of the CTA take the two halves of each chunk and
+// meet in red (which reuses vb once a plane is done); otherwise one thread
+// per row.  Returns false when a copy did
+// not complete in time (the CTA then stops using the buffers).
 template <typename T>
 __device__ bool sweeps3(const Box3& B, const T* __restrict__ F, const T* __restrict__ c2s, T* W, T* vb, T* cbuf,
-                        uint64_t* bar, uint32_t* par, int nr) {
+                        T* red, uint64_t* bar, uint32_t* par, int nr) {
     const int b = B.b, nc = B.nc;
     const int tid = threadIdx.x, nt = blockDim.x;
     const size_t ps = plane_stride(b);
@@ -326,7 +376,9 @@ __device__ bool sweeps3(const Box3& B, const T* __restrict__ F, const T* __restr
     const int nplane = 2 * B.np - 1;                  // forward planes, then backward planes np-2 .. 0
     const int total = nplane * nch;
     const size_t cap = stage_cap(CRr, b);              // entries per buffer
-    const int half = nt / 2, hr = tid % half, hq = tid / half;   // rows hr, hr + half, ..; rhs q = 2 hq, 2 hq + 1
+    const bool split = b <= nt / 2;
+    const int r = split ? tid % (nt / 2) : tid;        // row of this thread (active if r < b)
+    const int hf = split ? tid / (nt / 2) : 0;         // half of each chunk
     auto plane_of = [&](int p) { return p < B.np ? p : 2 * B.np - 2 - p; };
     auto issue = [&](int st) {
         const int j = plane_of(st / nch), ci = st % nch;
@@ -337,24 +389,29 @@ __device__ bool sweeps3(const Box3& B, const T* __restrict__ F, const T* __restr
         bulk_g2s(dst, F + (size_t)j * ps + (size_t)c0 * b, bytes, &bar[st & 1]);
     };
     if (tid == 0) issue(0);
-    T acc[2][2];
+    T acc[NR3];
     bool ok = true;
     for (int st = 0; st < total; ++st) {
         const int p = st / nch, ci = st % nch, j = plane_of(p);
         const bool fwd = p < B.np;
         if (ci == 0) {
-            for (int q = 0; q < nr; ++q)
-                for (int c = tid; c < b; c += nt) {
-                    T v;
-                    if (fwd) {
-                        v = W[q * nc + j * b + c];
-                        if (j > 0) v += c2s[(j - 1) * b + c] * W[q * nc + (j - 1) * b + c];
-                    } else {
-                        v = c2s[j * b + c] * W[q * nc + (j + 1) * b + c];
+            for (int c = tid; c < b; c += nt) {
+#pragma unroll
+                for (int q = 0; q < NR3; ++q) {
+                    T v = T(0);
+                    if (q < nr) {
+                        if (fwd) {
+                            v = W[q * nc + j * b + c];
+                            if (j > 0) v += c2s[(j - 1) * b + c] * W[q * nc + (j - 1) * b + c];
+                        } else {
+                            v = c2s[j * b + c] * W[q * nc + (j + 1) * b + c];
+                        }
                     }
-                    vb[q * b + c] = v;
+                    vb[c * NR3 + q] = v;
                 }
-            acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < NR3; ++q) acc[q] = T(0);
         }
         const bool done = mbar_wait(&bar[st & 1], par[st & 1]);
         par[st & 1] ^= 1u;
@@ -368,28 +425,43 @@ __device__ bool sweeps3(const Box3& B, const T* __restrict__ F, const T* __restr
         if (tid == 0 && st + 1 < total) issue(st + 1);
         const T* S = cbuf + (size_t)(st & 1) * cap;
         const int c0 = ci * CRr, cr = min(CRr, b - c0);
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = hr + rr * half;
-            if (r >= b) break;
-            for (int c = 0; c < cr; ++c) {
+        if (r < b) {
+            int ca = 0, cb = cr;
+            if (split) {
+                const int hc = (cr + 1) / 2;
+                ca = hf * hc;
+                cb = min(cr, ca + hc);
+            }
+            for (int c = ca; c < cb; ++c) {
                 const T sv = S[c * b + r];
+                const T* vq = vb + (size_t)(c0 + c) * NR3;
+                if (NR3 == 4 && std::is_same<T, float>::value) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(vq);
+                    acc[0] += sv * (T)v4.x;
+                    acc[1] += sv * (T)v4.y;
+                    acc[2] += sv * (T)v4.z;
+                    acc[3] += sv * (T)v4.w;
+                } else {
 #pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    const int q = 2 * hq + qq;
-                    if (q < nr) acc[rr][qq] += sv * vb[q * b + c0 + c];
+                    for (int q = 0; q < NR3; ++q) acc[q] += sv * vq[q];
                 }
             }
         }
         if (ci == nch - 1) {
-            for (int rr = 0; rr < 2; ++rr) {
-                const int r = hr + rr * half;
-                if (r >= b) break;
+            if (split) {
+                __syncthreads();   // red shares memory with vb: every thread is done reading vb
+                if (hf == 1 && r < b)
 #pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    const int q = 2 * hq + qq;
+                    for (int q = 0; q < NR3; ++q) red[r * NR3 + q] = acc[q];
+                __syncthreads();
+            }
+            if (hf == 0 && r < b) {
+#pragma unroll
+                for (int q = 0; q < NR3; ++q) {
                     if (q >= nr) continue;
-                    if (fwd) W[q * nc + j * b + r] = acc[rr][qq];
-                    else W[q * nc + j * b + r] += acc[rr][qq];
+                    const T v = split ? acc[q] + red[r * NR3 + q] : acc[q];
+                    if (fwd) W[q * nc + j * b + r] = v;
+                    else W[q * nc + j * b + r] += v;
                 }
             }
         }
@@ -411,7 +483,7 @@ __device__ __forceinline__ void atomic_max_f(unsigned int* a, float v) { atomicM
 // pairs) never reports non-convergence.  Returns the number of sweep pairs.
 template <typename T, typename Rhs>
 __device__ int solve3(const Box3& B, const MemberDev& md, const double* Tfm, const Ops3& O, const T* F, const T* c2s,
-                      double* X, T* W, T* vb, T* cbuf, uint64_t* bar, uint32_t* par, unsigned int* nrm, int nr,
+                      double* X, T* W, T* vb, T* cbuf, T* red, uint64_t* bar, uint32_t* par, unsigned int* nrm, int nr,
                       const Rhs& rhs, double tol, int max_ir, int* noconv, int* bad) {
     constexpr bool mixed = std::is_same<T, float>::value;
     const int nc = B.nc, tid = threadIdx.x, nt = blockDim.x;
@@ -429,7 +501,7 @@ __device__ int solve3(const Box3& B, const MemberDev& md, const double* Tfm, con
     __syncthreads();
     int it = 0;
     for (; it < mit; ++it) {
-        if (!sweeps3<T>(B, F, c2s, W, vb, cbuf, bar, par, nr)) {
+        if (!sweeps3<T>(B, F, c2s, W, vb, cbuf, red, bar, par, nr)) {
             if (threadIdx.x == 0) *bad = 1;
             __syncthreads();
             break;
@@ -534,8 +606,9 @@ __host__ __device__ inline size_t carve3_bytes(int tsz, int nx, int ny, int nz, 
     s += align16(nc);                                                          // nb
     s += align16(sizeof(double) * per) * 3;                                    // bT bB lam
     s += stored_rhs ? align16(sizeof(double) * nc) : 0;                       // bsrc
-    size_t fac = (mixed ? align16(sizeof(double) * nc) * 3 : 0) + align16(tsz * (size_t)b * b) +
-                 align16(tsz * (size_t)b) * 2 + 16;
+    const size_t ld = (size_t)plane_ld(b);
+    size_t fac = (mixed ? align16(sizeof(double) * nc) * 3 : 0) + align16(tsz * (size_t)b * ld) +
+                 align16(tsz * ld) + align16(tsz * (size_t)b) + 16;
     size_t sol = align16(tsz * 2 * stage_cap((int)crw, b));
     if (mixed) s += align16(tsz * NR3 * nc) + align16(tsz * NR3 * (size_t)b);  // W vb persistent
     else sol += align16(tsz * NR3 * nc) + align16(tsz * NR3 * (size_t)b);      // W vb in the solve overlay
@@ -552,7 +625,7 @@ struct Carve3 {
     double* bsrc;
     T *Sb, *rowbuf, *colbuf, *ipb;   // factor phase
     double* X;                       // solve phase (mixed: global scratch)
-    T *W, *vb, *cbuf;
+    T *W, *vb, *cbuf, *red;
     uint64_t* bar;
     double* macc;
     int* flags;
@@ -594,8 +667,9 @@ __device__ Carve3<T> carve3(unsigned char* base, const Box3& B, bool stored_rhs,
         C.O.c1 = (double*)take(sizeof(double) * nc);
         C.O.c2 = (double*)take(sizeof(double) * nc);
     }
-    C.Sb = (T*)take(sizeof(T) * b * b);
-    C.rowbuf = (T*)take(sizeof(T) * b);
+    const size_t ld = (size_t)plane_ld((int)b);
+    C.Sb = (T*)take(sizeof(T) * b * ld);
+    C.rowbuf = (T*)take(sizeof(T) * ld);
     C.colbuf = (T*)take(sizeof(T) * b);
     C.ipb = (T*)take(16);
     const size_t u1 = o;
@@ -607,6 +681,7 @@ __device__ Carve3<T> carve3(unsigned char* base, const Box3& B, bool stored_rhs,
         C.vb = (T*)take(sizeof(T) * NR3 * b);
     }
     if (o < u1) o = u1;
+    C.red = C.vb;   // the sweeps' partial sums reuse the sweep input (NR3 * b >= NR3 * rows)
     C.macc = (double*)take(sizeof(double) * NR3 * 6 * 3 * 2);
     C.flags = (int*)take(32);
     C.nrm = (unsigned int*)take(64);
@@ -698,11 +773,11 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
                         --qq;
                     }
             }
-            it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.bar, par, C.nrm, nr, rb, Mth.ir_tol,
+            it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.red, C.bar, par, C.nrm, nr, rb, Mth.ir_tol,
                            Mth.max_ir, &C.flags[1], &C.flags[2]);
         } else {
             RhsStored3 rs{C.bsrc};
-            it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.bar, par, C.nrm, nr, rs, Mth.ir_tol,
+            it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.red, C.bar, par, C.nrm, nr, rs, Mth.ir_tol,
                            Mth.max_ir, &C.flags[1], &C.flags[2]);
         }
         maxit = max(maxit, it);
@@ -849,7 +924,7 @@ __global__ void __launch_bounds__(T3) k_smooth3d(DevPtrs P, MethodDev Mth, const
     __syncthreads();
     const T* F = (const T*)P.fac + (size_t)item * P.fac_stride;
     RhsStored3 rs{C.bsrc};
-    const int it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.bar, par, C.nrm, 1, rs, Mth.ir_tol,
+    const int it = solve3<T>(B, md, P.Tf + md.cell_off * 3, C.O, F, C.c2s, C.X, C.W, C.vb, C.cbuf, C.red, C.bar, par, C.nrm, 1, rs, Mth.ir_tol,
                              Mth.max_ir, &C.flags[0], &C.flags[2]);
     __syncthreads();
     // overwrite (u, p) on Omega_i with the restriction
@@ -972,6 +1047,22 @@ size_t local3d_smem(int prec, int nx, int ny, int nz, bool part) {
 size_t smooth3d_smem(int prec, int nx, int ny, int nz) { return carve3_bytes(prec == 0 ? 8 : 4, nx, ny, nz, true); }
 
 // entries of one box factor (n_a2 planes of b x b)
+// The bulk copies of the sweeps need 16-byte aligned sources, destinations
+// and sizes: plane strides, chunk offsets and staging capacities of a box.
+bool stage3_aligned(int prec, int nx, int ny, int nz) {
+    int b, npl;
+    box3_dims(nx, ny, nz, &b, &npl);
+    const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
+    const int rows = stream_rows(b, prec != 0);
+    const size_t cap = stage_cap(rows, b);
+    const int nch = (b + rows - 1) / rows;
+    if ((plane_stride(b) * tsz) % 16 || (cap * tsz) % 16) return false;
+    if (nch > 1 && ((size_t)rows * b * tsz) % 16) return false;          // chunk starts
+    const size_t c0 = (size_t)(nch - 1) * rows;                            // last chunk
+    const size_t last = (((size_t)b - c0) * b * tsz + 15) & ~size_t(15);   // its rounded size
+    return last <= cap * tsz && c0 * b * tsz + last <= plane_stride(b) * tsz;
+}
+
 size_t factor3_entries(int nx, int ny, int nz) {
     int b, npl;
     box3_dims(nx, ny, nz, &b, &npl);

@@ -324,6 +324,116 @@ __device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cy
     }
 }
 
+// The same two sweeps with the whole CTA on one right-hand side: warp q
+// reduces columns [q kq, (q + 1) kq) of each line block; the partial sums of
+// the warps meet in red (double-buffered by line parity, so one barrier per
+// line), and every warp forms the next line's input in its own zw (32
+// entries per warp).  w: scaled right-hand side in, scaled solution out.
+template <typename T>
+__device__ void cta_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys, T* w, T* zw, T* red, int b,
+                           int nb) {
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nq = blockDim.x >> 5;
+    const int kq = (b + nq - 1) / nq, ka = wq * kq, kb = min(b, ka + kq);
+    T* z = zw + wq * 32;
+    int par = 0;
+    T cur = T(0);   // this lane's entry of the last finished line
+    // forward: w_j <- S_j^-1 (w_j + cys_{j-1} w_{j-1})
+    for (int j = 0; j < nb; ++j) {
+        if (lane < b) z[lane] = w[j * b + lane] + (j > 0 ? cys[(j - 1) * b + lane] * cur : T(0));
+        __syncwarp();
+        T acc = T(0);
+        if (lane < b) {
+            const T* S = Sinv + (size_t)j * b * b;
+            for (int k = ka; k < kb; ++k) acc += S[k * b + lane] * z[k];
+            red[(par * nq + wq) * 32 + lane] = acc;
+        }
+        __syncthreads();
+        if (lane < b) {
+            T s = T(0);
+            for (int q = 0; q < nq; ++q) s += red[(par * nq + q) * 32 + lane];
+            cur = s;
+            if (wq == 0) w[j * b + lane] = s;
+        }
+        par ^= 1;
+        __syncwarp();
+    }
+    // backward: w_j <- w_j + S_j^-1 cys_j w_{j+1}
+    for (int j = nb - 2; j >= 0; --j) {
+        if (lane < b) z[lane] = cys[j * b + lane] * cur;
+        // this line's forward value, read by every warp before warp 0 overwrites it
+        const T wf = lane < b ? w[j * b + lane] : T(0);
+        __syncwarp();
+        T acc = T(0);
+        if (lane < b) {
+            const T* S = Sinv + (size_t)j * b * b;
+            for (int k = ka; k < kb; ++k) acc += S[k * b + lane] * z[k];
+            red[(par * nq + wq) * 32 + lane] = acc;
+        }
+        __syncthreads();
+        if (lane < b) {
+            T s = wf;
+            for (int q = 0; q < nq; ++q) s += red[(par * nq + q) * 32 + lane];
+            cur = s;
+            if (wq == 0) w[j * b + lane] = s;
+        }
+        par ^= 1;
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// One right-hand side solved by the whole CTA (as warp_solve: FP64 form one
+// solve; mixed form FP32 sweeps + FP64 residual refinement, residual and
+// norms over all threads).  nrm: 2 unsigned ints of shared memory.
+template <typename T, typename Rhs>
+__device__ int cta_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys, double* x, T* w, T* zw, T* red,
+                         unsigned int* nrm, const Rhs& rhs, double tol, int max_ir, int* noconv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int b = B.nx, nb = B.ny;
+    if (std::is_same<T, double>::value) {
+        for (int c = tid; c < B.n; c += nt) w[c] = (T)rhs(B, O, c % b, c / b);
+        __syncthreads();
+        cta_sweeps<T>(Sinv, cys, w, zw, red, b, nb);
+        return 1;
+    }
+    if (tid < 2) nrm[tid] = 0u;
+    __syncthreads();
+    float bn = 0.f;
+    for (int c = tid; c < B.n; c += nt) {
+        const T wc = (T)(O.dsc[c] * rhs(B, O, c % b, c / b));
+        x[c] = 0.0;
+        w[c] = wc;
+        bn = fmaxf(bn, fabsf((float)wc));
+    }
+    for (int o = 16; o; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+    if ((tid & 31) == 0) atomicMax(&nrm[0], __float_as_uint(bn));
+    __syncthreads();
+    bn = __uint_as_float(nrm[0]);
+    int it = 0;
+    for (; it < max_ir; ++it) {
+        cta_sweeps<T>(Sinv, cys, w, zw, red, b, nb);
+        for (int c = tid; c < B.n; c += nt) x[c] += O.dsc[c] * (double)w[c];
+        if (tid == 0) nrm[1] = 0u;
+        __syncthreads();
+        float rn = 0.f;
+        for (int c = tid; c < B.n; c += nt) {
+            const int i = c % b, j = c / b;
+            const T wc = (T)(O.dsc[c] * (rhs(B, O, i, j) - apply_A(B, O, x, i, j)));
+            w[c] = wc;
+            rn = fmaxf(rn, fabsf((float)wc));
+        }
+        for (int o = 16; o; o >>= 1) rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, o));
+        if ((tid & 31) == 0) atomicMax(&nrm[1], __float_as_uint(rn));
+        __syncthreads();
+        rn = __uint_as_float(nrm[1]);
+        if ((double)rn <= tol * (double)bn || bn == 0.f) { ++it; break; }
+        if (it == max_ir - 1 && tid == 0) *noconv = 1;
+        __syncthreads();   // nrm[1] is reset at the top of the next step
+    }
+    __syncthreads();
+    return it;
+}
+
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 // Shared-memory carve-up ----------------------------------------------------

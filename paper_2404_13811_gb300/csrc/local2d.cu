@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
 // Step 7: one colour phase of a smoothing step (Sec. 3, Eqs. (sm_1)-(sm_2)).
 // One CTA (SM_WARPS warps) per subdomain of the colour; the kept factor is
 // staged into shared memory by the bulk-copy (TMA) engine while the
-// coefficients and Robin data are formed; warp 0 runs the sweeps.
+// coefficients and Robin data are formed; the whole CTA runs the sweeps
+// (each line's product split over the warps) and the FP64 residuals.
 // ---------------------------------------------------------------------------
 constexpr int SM_WARPS = 4;
 
@@ -211,7 +212,9 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     double* lam = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
     double* bsrc = (double*)take(sizeof(double) * n);
     T* cys = (T*)take(sizeof(T) * n);
-    T* zbuf = (T*)take(sizeof(T) * 32);
+    T* zbuf = (T*)take(sizeof(T) * 32 * SM_WARPS);       // one line input per warp
+    T* red = (T*)take(sizeof(T) * 2 * 32 * SM_WARPS);    // partial sums of the warps, two line parities
+    unsigned int* nrm = (unsigned int*)take(16);
     double* x = (double*)take(sizeof(double) * n);
     T* w = mixed ? (T*)take(sizeof(T) * n) : (T*)x;
     int* flags = (int*)take(64);
@@ -259,14 +262,13 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     }
     __syncthreads();
     int it = 0;
-    if (threadIdx.x < 32) {
-        const bool ok = mbar_wait(&bar, 0);
-        if (!ok) {
-            if (threadIdx.x == 0) flags[1] = 1;
-        } else {
-            RhsStored rs{bsrc};
-            it = warp_solve<T>(B, O, Sinv, cys, x, w, zbuf, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
-        }
+    // every thread reads the staged factor: all wait for the copy, and agree on a late one
+    const bool arrived = mbar_wait(&bar, 0);
+    if (!__syncthreads_or(!arrived)) {
+        RhsStored rs{bsrc};
+        it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
+    } else if (threadIdx.x == 0) {
+        flags[1] = 1;
     }
     __syncthreads();
     if (flags[1]) {
@@ -331,7 +333,8 @@ size_t smooth2d_smem(int prec, int nx, int ny) {
     size_t s = align16(tsz * n * nx);
     s += align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);
     s += align16(sizeof(double) * 2 * (nx + ny)) * 3 + align16(sizeof(double) * n);
-    s += align16(tsz * n) + align16(tsz * 32) + align16(sizeof(double) * n);
+    s += align16(tsz * n) + align16(tsz * 32 * SM_WARPS) + align16(tsz * 2 * 32 * SM_WARPS) + 16;
+    s += align16(sizeof(double) * n);
     if (prec != 0) s += align16(tsz * n);
     return s + 64;
 }

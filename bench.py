@@ -123,7 +123,32 @@ def algorithmic_flops(case):
             ni = sub[0] * sub[1]
             basis += nh * bx * bx + N * 4 * nh * bx + ni * sub[0] ** 2 + 4 * ni * sub[0]
             smooth += 4 * nh * bx
-    return {"local_basis": basis, "smooth_per_step": smooth}
+    # interface: every slab (one layer of subdomains along the last axis) is
+    # inverted once per factorisation, 2 n^3 flops for n unknowns
+    lu = 0.0
+    for iy in range(M[1]):
+        ns = sum(((ix > 0) + (ix < M[0] - 1) + (iy > 0) + (iy < M[1] - 1)) * npsi for ix in range(M[0]))
+        lu += 2.0 * ns ** 3
+    return {"local_basis": basis, "smooth_per_step": smooth, "interface_lu": lu}
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu measurement
+    (profiles/roofline_traffic.json), or None when the kernel's source has
+    changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh).get(kernel)
+    if not rec:
+        return None
+    hsh = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            hsh.update(fh.read())
+    return rec["bytes_per_launch"] if hsh.hexdigest() == rec["sha256"] else None
 
 
 def local_solves_per_step(case):
@@ -255,25 +280,28 @@ def run_gpu(args, rank, world):
            "h2d_bytes_per_step": int(2 * ncell * 8), "d2h_bytes_per_step": int(5 * ncell * 8),
            "includes": "create (plan, allocation, H2D of K and f) + build + interface + 8 smoothing steps + D2H of p, u"}
 
-    # roofline of the dominant kernel group
+    # roofline of the dominant kernel: the one with the most device time per
+    # step among the local basis kernels, the smoothing kernel and the slab LU
     flops = algorithmic_flops(case)
     nsm = sm_count()
     mhz = clocks.get("sm_mhz") or 1485.0
     peak32 = nsm * 128 * 2 * mhz * 1e6 / 1e12
     phase_ms = {k: v[0] / args.steps for k, v in tm.items()}
     launches = {k: v[1] / args.steps for k, v in tm.items()}
-    dom = max(("local_basis", "smooth"), key=lambda k: phase_ms[k])
-    if dom == "local_basis":
-        work = flops["local_basis"] / max(launches["local_basis"], 1)
-    else:
-        work = flops["smooth_per_step"] * N_SMOOTH / max(launches["smooth"], 1)
+    dom = max(("local_basis", "smooth", "interface_lu"), key=lambda k: phase_ms[k])
+    total = {"local_basis": flops["local_basis"], "smooth": flops["smooth_per_step"] * N_SMOOTH,
+             "interface_lu": flops["interface_lu"]}[dom]
+    kname = {"local_basis": "k_local2d<float>", "smooth": "k_smooth2d<float>", "interface_lu": "k_lu_inverse"}[dom]
+    work = total / max(launches[dom], 1)
     per_launch_ms = phase_ms[dom] / max(launches[dom], 1)
     achieved = work / (per_launch_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_local2d<float>" if dom == "local_basis" else "k_smooth2d<float>",
+    roof = {"bound": "alu", "kernel": kname,
             "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
-            "traffic": None,
-            "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock)",
-            "work_per_launch_flop": work, "launch_ms": per_launch_ms}
+            "traffic": measured_traffic(kname),
+            "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock; "
+                          "MEASURED_PEAKS.json holds no FP32 SIMT figure)",
+            "work_per_launch_flop": work, "launch_ms": per_launch_ms,
+            "work_rule": "factor n b^2 and 4 n b per solve (local kernels); 2 n^3 per slab inverse"}
     gpu_launches = int(sum(v[1] for v in tm.values()) / args.steps)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,

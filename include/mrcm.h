@@ -89,8 +89,11 @@ typedef struct {
  *                (Sec. 2.1, after Eq. (genRobin)).
  *   alpha_smooth the same for the smoothing solves (Sec. 3 uses 1).
  *   precision    MRCM_FP64 or MRCM_MIXED.
- *   ir_tol       relative residual (inf-norm) at which refinement stops
- *                (mixed local solves and the interface solve).
+ *   ir_tol       relative residual (inf-norm; Jacobi-scaled for the local
+ *                solves) that refinement must reach (mixed local solves and
+ *                the interface solve).  3D local solves refine on to their
+ *                residual floor: they stop at 1e-3 ir_tol, or below ir_tol
+ *                once the residual no longer halves per step.
  *   max_ir       maximum refinement steps. */
 typedef struct {
     int space;
@@ -235,11 +238,13 @@ int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl
  *   3 assembly of the MRCM-O solution
  *   4 smoothing colour phases (mrcm_smooth)
  *   5 replays of a captured step (mrcm_run with use_graph = 1)
+ *   6 the slab LU inverses alone (a part of phase 1)
  * mrcm_timings synchronises the stream and writes, for each of the first n
- * phases, the summed device time in ms (ms[i]) and the number of kernel
- * launches of this library in that phase (launches[i]); either pointer may be
- * NULL (phase 5 counts graph launches).  Launches are counted whether or not
- * profiling is enabled. */
+ * phases (n <= 7), the summed device time in ms (ms[i]) and the number of
+ * kernel launches of this library in that phase (launches[i]); either
+ * pointer may be NULL (phase 5 counts graph launches; phase 6 launches are
+ * also counted in phase 1).  Launches are counted whether or not profiling
+ * is enabled. */
 int mrcm_profile(mrcm_handle* h, int enable);
 int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n);
 

@@ -43,7 +43,7 @@ class mrcm_params(C.Structure):
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
            "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_set_permeability",
            "mrcm_adjoint", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_destroy", "mrcm_last_error"]
-PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph"]
+PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph", "interface_lu"]
 
 _lib = None
 
@@ -237,10 +237,11 @@ def mrcm_profile(h, enable):
 def mrcm_timings(h):
     """{phase: (device ms, launches)} since the last mrcm_profile call."""
     lib = load()
-    ms = (C.c_double * 6)()
-    ln = (C.c_longlong * 6)()
-    _check(lib, h, lib.mrcm_timings(h, ms, ln, 6))
-    return {PHASES[i]: (ms[i], ln[i]) for i in range(6)}
+    n = len(PHASES)
+    ms = (C.c_double * n)()
+    ln = (C.c_longlong * n)()
+    _check(lib, h, lib.mrcm_timings(h, ms, ln, n))
+    return {PHASES[i]: (ms[i], ln[i]) for i in range(n)}
 
 
 def mrcm_destroy(h):

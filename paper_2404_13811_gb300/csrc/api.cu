@@ -153,7 +153,7 @@ struct mrcm_handle {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
-    long long launches[6] = {0, 0, 0, 0, 0, 0};
+    long long launches[7] = {0, 0, 0, 0, 0, 0, 0};
     // captured step
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr, user_stream = nullptr;
@@ -739,8 +739,12 @@ static int issue_interface_factor(mrcm_handle* h) {
     for (size_t l = 0; l < h->levels.size(); ++l) {
         Level& L = h->levels[l];
         if (L.count == 0) continue;
-        CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
+        {
+            Phase lu(h, 6);
+            CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
+        }
         h->launches[1] += 1;
+        h->launches[6] += 1;
         if (l + 1 < h->levels.size()) {
             CUDA_TRY(h, bcr_elim(I, h->d_elims + L.off, L.count, h->elim_smem, st));
             h->launches[1] += 1;
@@ -1269,13 +1273,13 @@ int mrcm_profile(mrcm_handle* h, int enable) {
 int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (auto& r : h->ev_rec) {
         float t = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&t, r.second.first, r.second.second));
-        if (r.first >= 0 && r.first < 6) acc[r.first] += t;
+        if (r.first >= 0 && r.first < 7) acc[r.first] += t;
     }
-    for (int i = 0; i < n && i < 6; ++i) {
+    for (int i = 0; i < n && i < 7; ++i) {
         if (ms) ms[i] = acc[i];
         if (launches) launches[i] = h->launches[i];
     }

@@ -364,7 +364,7 @@ __host__ __device__ inline size_t adj_carve_bytes(int nx, int ny, int nw, bool p
     const size_t per = 2 * (size_t)(nx + ny);
     size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);   // cd cx cy dsc hk
     s += align16(sizeof(double) * per) * 3;                                           // bT bB gbT
-    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) + align16(sizeof(T) * nx * nx);
+    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) * 2 + align16(sizeof(T) * nx * nx);
     s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * nw);
     s += part ? align16(sizeof(double) * n) : 0;
     s += align16(sizeof(double) * n) * 2;                                             // gcx gcy
@@ -373,7 +373,7 @@ __host__ __device__ inline size_t adj_carve_bytes(int nx, int ny, int nw, bool p
 }
 
 template <typename T, int BW>
-__global__ void __launch_bounds__(128) k_adj_local2d(DevPtrs P, MethodDev Mth, AdjPtrs A, const Job* jobs) {
+__global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth, AdjPtrs A, const Job* jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool mixed = std::is_same<T, float>::value;
     const int nw = blockDim.x >> 5;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(128) k_adj_local2d(DevPtrs P, MethodDev Mth, A
     T* Sinv = (T*)take(sizeof(T) * n * B.nx);
     T* cys = (T*)take(sizeof(T) * n);
     T* Sbuf = (T*)take(sizeof(T) * B.nx * B.nx);
-    T* rowbuf = (T*)take(sizeof(T) * 32);
+    T* cxs = (T*)take(sizeof(T) * n);
     T* zall = (T*)take(sizeof(T) * 32 * nw);
     double* bsrc = basis ? nullptr : (double*)take(sizeof(double) * n);
     double* gcx = (double*)take(sizeof(double) * n);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(128) k_adj_local2d(DevPtrs P, MethodDev Mth, A
     for (int t = threadIdx.x; t < per; t += blockDim.x) gbT[t] = 0.0;
     build_ops(B, md, P, O);
     fill_scale(B, O, mixed);
-    factor_box<T, BW>(B, O, Sinv, cys, Sbuf, rowbuf, &flags[0]);
+    factor_box<T, BW>(B, O, Sinv, cys, cxs, Sbuf, &flags[0]);
     if (flags[0] && threadIdx.x == 0) {
         atomicOr(&P.status[0], ST_NOT_SPD);
         atomicExch(&P.status[2], job.item);

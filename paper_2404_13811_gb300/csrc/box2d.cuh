@@ -116,10 +116,14 @@ __device__ __forceinline__ double apply_A(const Box& B, const Ops& O, const doub
     return s;
 }
 
-// In-register Gauss-Jordan inverse of an SPD b x b block (row i in lane i).
-// Pivot reciprocals in FP64.  Writes Sout (row-major, b x b).
+// In-register Gauss-Jordan inverse of an SPD b x b block (row i in lane i),
+// SPD so no pivoting.  The pivot row reaches every lane by shuffles from lane
+// k; the pivot lane and the other lanes update with selects (no divergent
+// paths), so a step is one chain of b shuffles and b FMAs.  Pivot
+// reciprocals: the correctly rounded FP32 reciprocal in the FP32 form, FP64
+// otherwise.  Writes Sout (row-major, b x b).
 template <typename T, int BW>
-__device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
+__device__ void gj_invert(const T* S, T* Sout, int b, int* bad) {
     const int lane = threadIdx.x & 31;
     T a[BW];
 #pragma unroll
@@ -127,27 +131,27 @@ __device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
 #pragma unroll
     for (int k = 0; k < BW; ++k) {
         if (k < b) {
-            if (lane == k) {
+            T rv[BW];
 #pragma unroll
-                for (int c = 0; c < BW; ++c) rowbuf[c] = a[c];
-            }
-            __syncwarp();
-            double piv = (double)rowbuf[k];
-            if (!(piv > 0.0)) {
+            for (int c = 0; c < BW; ++c) rv[c] = __shfl_sync(0xffffffffu, a[c], k);
+            T piv = rv[k];
+            if (!(piv > T(0))) {
                 if (lane == 0) *bad = 1;
-                piv = 1.0;
+                piv = T(1);
             }
-            // FP32 form: __frcp_rn is the FP64 reciprocal rounded to FP32
-            const T ip = std::is_same<T, float>::value ? (T)__frcp_rn((float)piv) : (T)rcp64(piv);
-            if (lane == k) {
+            T ip;
+            if constexpr (std::is_same<T, float>::value) ip = __frcp_rn(piv);
+            else ip = rcp64(piv);
+            // one FMA per entry: the pivot lane computes 0 - (-ip) rv = ip rv,
+            // the others a - f rv; column k takes ip / -f
+            const bool isk = lane == k;
+            const T f = a[k] * ip;
+            const T fl = isk ? -ip : f;
 #pragma unroll
-                for (int c = 0; c < BW; ++c) a[c] = (c == k) ? ip : a[c] * ip;
-            } else {
-                const T fip = a[k] * ip;
-#pragma unroll
-                for (int c = 0; c < BW; ++c) a[c] = (c == k) ? -fip : a[c] - fip * rowbuf[c];
+            for (int c = 0; c < BW; ++c) {
+                const T base = isk ? T(0) : a[c];
+                a[c] = (c == k) ? (isk ? ip : -f) : base - fl * rv[c];
             }
-            __syncwarp();
         }
     }
     if (lane < b) {
@@ -158,35 +162,52 @@ __device__ void gj_invert(const T* S, T* Sout, int b, T* rowbuf, int* bad) {
     __syncwarp();
 }
 
-// Block LDL^T factorisation: Sinv[j] = S_j^{-1}.  cys = scaled line coupling
-// (type T).  All threads participate.
+// Block LDL^T factorisation: Sinv[j] = S_j^{-1}.  cys / cxs: the scaled line
+// / in-line couplings (type T, formed once).  The off-diagonal entries of
+// each line Schur block are formed in T; its diagonal
+// d_i - c_i^2 (S_{j-1}^{-1})_ii, where the cancellation is, in FP64 by one
+// warp.  All threads participate; warp 0 inverts.
 template <typename T, int BW>
-__device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* Sbuf, T* rowbuf, int* bad) {
-    const int b = B.nx, nb = B.ny;
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+__device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* cxs, T* Sbuf, int* bad) {
+    const int b = B.nx, nb = B.ny, bb = b * b;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = tid; c < B.n; c += nt) {
         cys[c] = (T)(O.cy[c] * O.dsc[c] * ((c + b < B.n) ? O.dsc[c + b] : 0.0));
+        cxs[c] = (T)(-O.cx[c] * O.dsc[c] * ((c % b) < b - 1 ? O.dsc[c + 1] : 0.0));
+    }
     __syncthreads();
+    const int i0 = tid / b, k0 = tid - i0 * b;
+    const int di = nt / b, dk = nt - di * b;
     for (int j = 0; j < nb; ++j) {
-        for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-            const int i = t / b, k = t - (t / b) * b;
-            const int ci = j * b + i, ck = j * b + k;
-            if (i == k) {
-                double s = O.cd[ci] * O.dsc[ci] * O.dsc[ci];
-                if (j > 0) {
-                    const double cc = (double)cys[ci - b];
-                    s -= cc * cc * (double)Sinv[((j - 1) * b + i) * b + i];
-                }
-                Sbuf[t] = (T)s;
-            } else {
+        const T* Sp = Sinv + (size_t)(j > 0 ? j - 1 : 0) * bb;
+        int i = i0, k = k0;
+        for (int t = tid; t < bb; t += nt) {
+            if (i != k) {
+                const int ci = j * b + i, ck = j * b + k;
                 T s = T(0);
-                if (k == i + 1) s = (T)(-O.cx[ci] * O.dsc[ci] * O.dsc[ck]);
-                if (k == i - 1) s = (T)(-O.cx[ck] * O.dsc[ci] * O.dsc[ck]);
-                if (j > 0) s -= cys[ci - b] * Sinv[((j - 1) * b + i) * b + k] * cys[ck - b];
+                if (k == i + 1) s = cxs[ci];
+                else if (k == i - 1) s = cxs[ck];
+                if (j > 0) s -= cys[ci - b] * Sp[i * b + k] * cys[ck - b];
                 Sbuf[t] = s;
             }
+            k += dk;
+            i += di;
+            if (k >= b) {
+                k -= b;
+                ++i;
+            }
+        }
+        if (tid < b) {
+            const int ci = j * b + tid;
+            double s = O.cd[ci] * O.dsc[ci] * O.dsc[ci];
+            if (j > 0) {
+                const double cc = (double)cys[ci - b];
+                s -= cc * cc * (double)Sp[tid * b + tid];
+            }
+            Sbuf[tid * b + tid] = (T)s;
         }
         __syncthreads();
-        if (threadIdx.x < 32) gj_invert<T, BW>(Sbuf, Sinv + (size_t)j * b * b, b, rowbuf, bad);
+        if (tid < 32) gj_invert<T, BW>(Sbuf, Sinv + (size_t)j * bb, b, bad);
         __syncthreads();
     }
 }
@@ -442,8 +463,8 @@ struct Carve {
     Ops O;
     T* Sinv;
     T* cys;
+    T* cxs;
     T* Sbuf;
-    T* rowbuf;
     T* zbuf;   // NWARP * 32
     double* bsrc; // n: fixed right-hand side of the particular problem
     double* X; // nrhs * n
@@ -456,7 +477,7 @@ __host__ __device__ inline size_t carve_bytes(int nx, int ny, int nrhs) {
     const size_t n = (size_t)nx * ny;
     size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);  // cd cx cy dsc hk
     s += align16(sizeof(double) * 2 * (nx + ny)) * 2;                                 // bT bB
-    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) + align16(sizeof(T) * nx * nx);
+    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) * 2 + align16(sizeof(T) * nx * nx);
     s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * NWARP) + align16(sizeof(double) * n);
     if (std::is_same<T, float>::value) s += align16(sizeof(double) * n * nrhs);
     s += align16(sizeof(T) * n * nrhs);
@@ -478,8 +499,8 @@ __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
     C.O.bB = (double*)take(sizeof(double) * 2 * (nx + ny));
     C.Sinv = (T*)take(sizeof(T) * n * nx);
     C.cys = (T*)take(sizeof(T) * n);
+    C.cxs = (T*)take(sizeof(T) * n);
     C.Sbuf = (T*)take(sizeof(T) * nx * nx);
-    C.rowbuf = (T*)take(sizeof(T) * 32);
     C.zbuf = (T*)take(sizeof(T) * 32 * NWARP);
     C.bsrc = (double*)take(sizeof(double) * n);
     if (std::is_same<T, float>::value) C.X = (double*)take(sizeof(double) * n * nrhs);

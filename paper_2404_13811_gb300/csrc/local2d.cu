@@ -28,7 +28,7 @@
 // Steps 1, 2, 4 and 6 of Algorithm 1 for 2D subdomains.
 // ---------------------------------------------------------------------------
 template <typename T, int BW>
-__global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth, const Job* jobs) {
+__global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev Mth, const Job* jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool mixed = std::is_same<T, float>::value;
     const Job job = jobs[blockIdx.x];
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_local2d(DevPtrs P, MethodDev Mth
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
     build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
-    factor_box<T, BW>(B, C.O, C.Sinv, C.cys, C.Sbuf, C.rowbuf, &C.flags[0]);
+    factor_box<T, BW>(B, C.O, C.Sinv, C.cys, C.cxs, C.Sbuf, &C.flags[0]);
 
     // keep the factor for the smoothing steps
     const bool keep = (job.type == JOB_SFACT) || (job.type == JOB_BASIS && Mth.same_alpha);

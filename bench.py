@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle check and CPU baseline")
+    ap.add_argument("--workload", default="channel2d",
+                    choices=["channel2d", "small", "layered3d", "ensemble", "adjoint"],
+                    help="channel2d: the benchmark line; the others print a timing line for another "
+                         "workload (64x64 quarter five-spot, 60x220x85 layered 3D, 256-member ensemble, "
+                         "256x256 gradient)")
     return ap.parse_args()
 
 
@@ -337,6 +342,97 @@ def run_gpu(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# timing lines of the other workloads (not the benchmark line)
+# ---------------------------------------------------------------------------
+def run_other(args):
+    import torch
+    from paper_2404_13811_gb300 import build as B
+    from paper_2404_13811_gb300 import inputs as I
+    from paper_2404_13811_gb300.solver import MRCM
+
+    B.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
+
+    def timeit(fn, K, W):
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(K):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / K
+
+    def phases(s, ns):
+        s.profile(True)
+        s.build_basis()
+        s.solve_interface()
+        s.smooth(ns)
+        tm = s.timings()
+        s.profile(False)
+        return {k: round(v[0], 3) for k, v in tm.items() if v[0] > 0}
+
+    w = args.workload
+    line = {"workload": w, "unit": "cells/s", "steps": args.steps, "warmup": args.warmup,
+            "l2": "flushed (512 MB write) between timed steps", "data": "synthetic"}
+    if w in ("small", "layered3d", "ensemble"):
+        cases = I.config_ensemble() if w == "ensemble" else [I.config_small() if w == "small" else I.config_layered3d()]
+        probs = [c.problem for c in cases]
+        parts = [c.partition for c in cases]
+        pm = cases[0].params
+        cells = sum(p.ncells for p in probs)
+        line.update({"members": len(cases), "cells": cells, "n_smooth": pm.n_smooth,
+                     "step": "mrcm_run: the whole step replayed as one captured CUDA graph"})
+        for precision in ("mixed", "fp64"):
+            s = MRCM(probs if len(probs) > 1 else probs[0], parts if len(parts) > 1 else parts[0], space=pm.space,
+                     alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth, precision=precision, stream=stream)
+            ms = timeit(lambda: s.run(pm.n_smooth, graph=True), args.steps, args.warmup)
+            line[precision] = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "phase_ms_eager": phases(s, pm.n_smooth),
+                               "subdomains": s.stats()["subdomains"]}
+            s.close()
+    else:
+        case = I.config_adjoint()
+        prob, part, pm = case.problem, case.partition, case.params
+        sinks = np.array([ix + prob.n[0] * iy for (ix, iy) in case.extra["sinks"]])
+        # the loss target: the forward solution for the second K (an input of the timing)
+        t = MRCM(case.extra["target_problem"], part, space=pm.space, precision="fp64", stream=stream)
+        t.run(pm.n_smooth)
+        ut = t.state()[1][torch.as_tensor(sinks, device="cuda")]
+        t.close()
+        line.update({"cells": prob.ncells, "n_smooth": pm.n_smooth,
+                     "loss": "sum over the 4 faces of 8 sink cells of (u - u_target)^2"})
+        for precision in ("mixed", "fp64"):
+            s = MRCM(prob, part, space=pm.space, alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth,
+                     precision=precision, stream=stream)
+            rows = torch.as_tensor(sinks, device="cuda")
+
+            def fwd():
+                s.run(pm.n_smooth)
+
+            def grad():
+                u = s.state()[1]
+                gu = torch.zeros_like(u)
+                gu[rows] = 2.0 * (u[rows] - ut)
+                return s.adjoint(None, gu)
+
+            fwd()
+            ms_f = timeit(fwd, args.steps, args.warmup)
+            ms_g = timeit(grad, args.steps, args.warmup)
+            line[precision] = {"forward_ms": ms_f, "adjoint_ms": ms_g, "adjoint_over_forward": ms_g / ms_f,
+                               "value": prob.ncells / ((ms_f + ms_g) * 1e-3)}
+            s.close()
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
@@ -378,6 +474,8 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload != "channel2d":
+        run_other(args)
     else:
         run_gpu(args, rank, world)
     if world > 1:

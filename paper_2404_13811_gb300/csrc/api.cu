@@ -18,7 +18,7 @@
 #include "mrcm_internal.cuh"
 
 // launchers defined in the other translation units
-size_t local2d_smem(int prec, int nx, int ny, int nrhs);
+size_t local2d_smem(int prec, int nx, int ny, int nrhs, bool part);
 size_t smooth2d_smem(int prec, int nx, int ny);
 cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int bw,
                            size_t smem, cudaStream_t s);
@@ -458,7 +458,8 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         auto add = [&](int type, int nx, int ny, int nrhs) {
             int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
             byw[bw].push_back(Job{s, type});
-            smem_w[bw] = std::max(smem_w[bw], local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1)));
+            smem_w[bw] = std::max(smem_w[bw],
+                                  local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1), type == JOB_PART));
         };
         add(JOB_BASIS, bx, by, sd.nbasis);
         add(JOB_PART, ix, iy, 1);

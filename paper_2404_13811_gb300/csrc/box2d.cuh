@@ -62,8 +62,10 @@ __device__ void build_ops(const Box& B, const MemberDev& md, const DevPtrs& P, O
         const long long g = (B.lo[0] + i) + (long long)nxg * (B.lo[1] + j);
         O.cx[c] = i < B.nx - 1 ? Tf[g * 3 + 0] : 0.0;
         O.cy[c] = j < B.ny - 1 ? Tf[g * 3 + 1] : 0.0;
-        O.hk[2 * c] = hkg[g * 3 + 0];
-        O.hk[2 * c + 1] = hkg[g * 3 + 1];
+        if (O.hk) {   // null where the kernel reads h / 2K from global memory
+            O.hk[2 * c] = hkg[g * 3 + 0];
+            O.hk[2 * c + 1] = hkg[g * 3 + 1];
+        }
     }
     const double ax = md.h[1], ay = md.h[0];  // face areas (normal to x, normal to y)
     for (int sid = 0; sid < 4; ++sid) {
@@ -473,19 +475,23 @@ struct Carve {
 };
 
 template <typename T>
-__host__ __device__ inline size_t carve_bytes(int nx, int ny, int nrhs) {
+// (the basis / particular kernel keeps no h / 2K array -- it reads the few
+// values it needs at the Gamma faces from global memory -- and a stored
+// right-hand side only for the particular problem, so that two CTAs of the
+// 24 x 24 basis boxes fit on one SM)
+__host__ __device__ inline size_t carve_bytes(int nx, int ny, int nrhs, bool part) {
     const size_t n = (size_t)nx * ny;
-    size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);  // cd cx cy dsc hk
+    size_t s = align16(sizeof(double) * n) * 4;                                      // cd cx cy dsc
     s += align16(sizeof(double) * 2 * (nx + ny)) * 2;                                 // bT bB
     s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) * 2 + align16(sizeof(T) * nx * nx);
-    s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * NWARP) + align16(sizeof(double) * n);
+    s += align16(sizeof(T) * 32 * NWARP) + (part ? align16(sizeof(double) * n) : 0);
     if (std::is_same<T, float>::value) s += align16(sizeof(double) * n * nrhs);
     s += align16(sizeof(T) * n * nrhs);
     return s + 64;
 }
 
 template <typename T>
-__device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
+__device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs, bool part) {
     Carve<T> C;
     const size_t n = (size_t)nx * ny;
     size_t o = 0;
@@ -494,7 +500,7 @@ __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
     C.O.cx = (double*)take(sizeof(double) * n);
     C.O.cy = (double*)take(sizeof(double) * n);
     C.O.dsc = (double*)take(sizeof(double) * n);
-    C.O.hk = (double*)take(sizeof(double) * 2 * n);
+    C.O.hk = nullptr;
     C.O.bT = (double*)take(sizeof(double) * 2 * (nx + ny));
     C.O.bB = (double*)take(sizeof(double) * 2 * (nx + ny));
     C.Sinv = (T*)take(sizeof(T) * n * nx);
@@ -502,7 +508,7 @@ __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs) {
     C.cxs = (T*)take(sizeof(T) * n);
     C.Sbuf = (T*)take(sizeof(T) * nx * nx);
     C.zbuf = (T*)take(sizeof(T) * 32 * NWARP);
-    C.bsrc = (double*)take(sizeof(double) * n);
+    C.bsrc = part ? (double*)take(sizeof(double) * n) : nullptr;
     if (std::is_same<T, float>::value) C.X = (double*)take(sizeof(double) * n * nrhs);
     C.W = (T*)take(sizeof(T) * n * nrhs);
     if (std::is_same<T, double>::value) C.X = (double*)C.W;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
     }
     __syncthreads();
     const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (job.type == JOB_PART ? 1 : 0);
-    Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? min(nrhs, NWARP) : 1);
+    Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? min(nrhs, NWARP) : 1, job.type == JOB_PART);
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
     build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
                 else        { i = offx + e; j = (sid == 2) ? offy : offy + nIy - 1; }
                 const int cL = j * B.nx + i;
                 const double pL = x[cL];
-                const double hkL = C.O.hk[2 * cL + a];
+                const double hkL = P.hk[(md.cell_off + (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j)) * 3 + a];
                 bool inner;
                 int cR;
                 double Tf;
@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-size_t local2d_smem(int prec, int nx, int ny, int nrhs) {
-    return prec == 0 ? carve_bytes<double>(nx, ny, nrhs) : carve_bytes<float>(nx, ny, nrhs);
+size_t local2d_smem(int prec, int nx, int ny, int nrhs, bool part) {
+    return prec == 0 ? carve_bytes<double>(nx, ny, nrhs, part) : carve_bytes<float>(nx, ny, nrhs, part);
 }
 
 size_t smooth2d_smem(int prec, int nx, int ny) {
@@ -346,6 +346,9 @@ static cudaError_t launch_local_t(const DevPtrs& P, const MethodDev& M, const Jo
     static size_t set_smem = 0;
     if (smem > set_smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        // all of the unified L1 / shared storage as shared memory (two CTAs per SM)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }

@@ -622,8 +622,9 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         while (elim_cw > 32 && elim_smem_bytes((int)nmv, elim_cw) > 227 * 1024) elim_cw = (elim_cw + 1) / 2;
         h->elim_smem = elim_smem_bytes((int)nmv, elim_cw);
         if (h->elim_smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface coupling blocks too large");
-        while (xch > 4 && lu_smem(npad, xch) > 227 * 1024) xch /= 2;
-        if (lu_smem(npad, xch) > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface slabs too large");
+        // 1 KB of the 227 KB per block is left to the slab LU's static shared memory
+        while (xch > 4 && lu_smem(npad, xch) > 226 * 1024) xch /= 2;
+        if (lu_smem(npad, xch) > 226 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "interface slabs too large");
     }
     // elimination levels over all members
     int maxS = 0;

@@ -18,6 +18,8 @@ namespace cg = cooperative_groups;
 constexpr int GJ_NB = 32;   // panel width
 constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
 constexpr int GJ_THREADS = 512;
+constexpr int GJ_NB_WARPS = GJ_THREADS / 32;
+constexpr int PUB_PAR = GJ_NB_WARPS * GJ_NB;   // one parity of the slab LU's published panel rows
 #ifndef MRCM_PANEL_WARPS
 #define MRCM_PANEL_WARPS 8
 #endif
@@ -673,6 +675,7 @@ __device__ void tile_update(const float* __restrict__ P, float* __restrict__ X, 
     }
 }
 
+template <int RPT>
 __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -690,8 +693,9 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     int* piv = (int*)(Upy + max(GJ_NB * ncmax, np));  // np
     int* ownc = piv + np;                      // ncmax
     int* qpos = ownc + ncmax;                  // np
-    __shared__ float redv[32];
-    __shared__ int redi[32];
+    float* pub = reinterpret_cast<float*>(qpos + np);   // 2 x PUB_PAR candidate rows published per column
+    unsigned* pkey = reinterpret_cast<unsigned*>(pub + 2 * PUB_PAR);   // 2 x GJ_NB_WARPS pivot keys
+    unsigned* pidx = pkey + 2 * GJ_NB_WARPS;                              // and their rows
     __shared__ int nown;
     __shared__ int aff[2 * GJ_NB];
     __shared__ int naff;
@@ -720,45 +724,115 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                 for (int r = k0 + lane; r < np; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
         cluster.sync();
         if (!active) continue;
-        // panel factorisation with partial pivoting on warps 0-3 (named barrier 1)
-        if (warp < PANEL_WARPS) {
-            const int pt = tid, pn = PANEL_WARPS * 32;
-            for (int c = 0; c < b; ++c) {
-                const int r0 = k0 + c;
-                float best = -1.f;
-                int bi = r0;
-                for (int r = r0 + pt; r < np; r += pn) {
-                    const float v = fabsf(Ps[c * np + r]);
-                    if (v > best) { best = v; bi = r; }
-                }
-                for (int o = 16; o; o >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-                }
-                if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
-                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
-                float v = redv[0];
-                int p = redi[0];
+        // panel factorisation with partial pivoting.  Every thread keeps its
+        // RPT panel rows (slots k0 + tid + 512 i) in registers for the whole
+        // panel and never moves them; it tracks the logical row each slot
+        // holds, so a row interchange is two integer updates.  The registers
+        // rotate left after every column, so the pivot column is always x[0]
+        // and the column loop stays one short body.  One barrier per column:
+        // before it each warp reduces its pivot candidate (|a| as an unsigned
+        // key, smallest logical row on ties) by redux and publishes that row;
+        // after it every warp picks the winner among the warps' keys.  The
+        // published rows are double-buffered by the column's parity.  Each
+        // step leaves column c of every slot in Ps; the slots are put into
+        // logical row order once the panel is done.
+        {
+            float x[RPT][GJ_NB];
+            int lp[RPT];
 #pragma unroll
-                for (int w = 1; w < PANEL_WARPS; ++w)
-                    if (redv[w] > v || (redv[w] == v && redi[w] < p)) { v = redv[w]; p = redi[w]; }
-                if (pt == 0) piv[r0] = p;
-                if (p != r0 && pt < b) {
-                    const float t0 = Ps[pt * np + r0];
-                    Ps[pt * np + r0] = Ps[pt * np + p];
-                    Ps[pt * np + p] = t0;
+            for (int i = 0; i < RPT; ++i) {
+                const int r = k0 + tid + i * nt;
+                lp[i] = r;
+#pragma unroll
+                for (int cc = 0; cc < GJ_NB; ++cc) x[i][cc] = (r < np && cc < b) ? Ps[cc * np + r] : 0.f;
+            }
+#pragma unroll 1
+            for (int c = 0; c < b; ++c) {
+                const int r0 = k0 + c, par = c & 1;
+                float* pb = pub + par * PUB_PAR;            // [warp][GJ_NB] candidate rows
+                unsigned key = 0u, kr = 0xffffffffu;
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    if (lp[i] >= r0 && lp[i] < np) {
+                        const float v = fabsf(x[i][0]);
+                        const unsigned kb = v == v ? __float_as_uint(v) : 0u;   // NaN never wins over a number
+                        if (kr == 0xffffffffu || kb > key || (kb == key && (unsigned)lp[i] < kr)) {
+                            key = kb;
+                            kr = (unsigned)lp[i];
+                        }
+                    }
                 }
-                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
-                float a = Ps[c * np + r0];
-                if (a == 0.f) { singular = true; a = 1e-30f; }
-                const float ia = 1.f / a;
-                for (int r = r0 + 1 + pt; r < np; r += pn) {
-                    const float l = Ps[c * np + r] * ia;
-                    Ps[c * np + r] = l;
-                    for (int cc = c + 1; cc < b; ++cc) Ps[cc * np + r] -= l * Ps[cc * np + r0];
+                const unsigned m = __reduce_max_sync(0xffffffffu, key);
+                const unsigned wi = __reduce_min_sync(0xffffffffu, (kr != 0xffffffffu && key == m) ? kr : 0xffffffffu);
+#pragma unroll
+                for (int i = 0; i < RPT; ++i)
+                    if ((unsigned)lp[i] == wi) {
+                        float4* dst = reinterpret_cast<float4*>(pb + warp * GJ_NB);
+#pragma unroll
+                        for (int q4 = 0; q4 < GJ_NB / 4; ++q4)
+                            dst[q4] = make_float4(x[i][4 * q4], x[i][4 * q4 + 1], x[i][4 * q4 + 2], x[i][4 * q4 + 3]);
+                    }
+                if (lane == 0) { pkey[par * GJ_NB_WARPS + warp] = m; pidx[par * GJ_NB_WARPS + warp] = wi; }
+                __syncthreads();
+                const unsigned km = lane < GJ_NB_WARPS ? pkey[par * GJ_NB_WARPS + lane] : 0u;
+                const unsigned ki = lane < GJ_NB_WARPS ? pidx[par * GJ_NB_WARPS + lane] : 0xffffffffu;
+                const unsigned bm = __reduce_max_sync(0xffffffffu, ki != 0xffffffffu ? km : 0u);
+                const unsigned p = __reduce_min_sync(0xffffffffu, (ki != 0xffffffffu && km == bm) ? ki : 0xffffffffu);
+                const unsigned wb = __ballot_sync(0xffffffffu, ki == p && p != 0xffffffffu);
+                if (wb == 0u) {
+                    // no candidate anywhere (cannot happen while r0 < np): keep the order, flag it
+                    singular = true;
+                    if (tid == 0) piv[r0] = r0;
+                } else {
+                    const int pw = __ffs(wb) - 1;
+                    if (tid == 0) piv[r0] = (int)p;
+                    const float4* src = reinterpret_cast<const float4*>(pb + pw * GJ_NB);
+                    float a = pb[pw * GJ_NB];
+                    if (a == 0.f) { singular = true; a = 1e-30f; }
+                    const float ia = 1.f / a;
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) {
+                        if ((unsigned)lp[i] == p) lp[i] = r0;
+                        else if (lp[i] == r0) lp[i] = (int)p;
+                        if (lp[i] > r0 && lp[i] < np) {
+                            const float l = x[i][0] * ia;
+                            x[i][0] = l;
+#pragma unroll
+                            for (int q4 = 0; q4 < GJ_NB / 4; ++q4) {
+                                const float4 t = src[q4];
+                                if (q4 > 0) x[i][4 * q4] -= l * t.x;
+                                x[i][4 * q4 + 1] -= l * t.y;
+                                x[i][4 * q4 + 2] -= l * t.z;
+                                x[i][4 * q4 + 3] -= l * t.w;
+                            }
+                        }
+                    }
                 }
-                asm volatile("bar.sync 1, %0;" ::"r"(pn) : "memory");
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    const int sl = k0 + tid + i * nt;
+                    if (sl < np) Ps[c * np + sl] = x[i][0];
+#pragma unroll
+                    for (int cc = 0; cc < GJ_NB - 1; ++cc) x[i][cc] = x[i][cc + 1];
+                    x[i][GJ_NB - 1] = 0.f;
+                }
+            }
+            // slots into logical row order
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int sl = k0 + tid + i * nt;
+#pragma unroll
+                for (int cc = 0; cc < GJ_NB; ++cc) x[i][cc] = (sl < np && cc < b) ? Ps[cc * np + sl] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                if (k0 + tid + i * nt < np) {
+#pragma unroll
+                    for (int cc = 0; cc < GJ_NB; ++cc)
+                        if (cc < b) Ps[cc * np + lp[i]] = x[i][cc];
+                }
             }
         }
         __syncthreads();
@@ -942,8 +1016,8 @@ size_t lu_smem(int np, int xch) {
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
     const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)xch * np);
-    return sizeof(float) * ((size_t)GJ_NB * np + xs + up) +
-           sizeof(int) * ((size_t)np + ncmax + np) + 16;
+    return sizeof(float) * ((size_t)GJ_NB * np + xs + up + 2 * PUB_PAR) +
+           sizeof(int) * ((size_t)np + ncmax + np + 4 * GJ_NB_WARPS) + 16;
 }
 
 
@@ -967,15 +1041,19 @@ static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, si
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
     const size_t smem = lu_smem(I.npad, I.xch);
-    static size_t set_smem = 0;
-    if (smem > set_smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // panel rows per thread: one for slabs of up to GJ_THREADS unknowns, else two
+    const bool two = I.npad > GJ_THREADS;
+    const void* kern = two ? (const void*)k_lu_inverse<2> : (const void*)k_lu_inverse<1>;
+    static size_t set_smem[2] = {0, 0};
+    if (smem > set_smem[two]) {
+        cudaError_t e = two ? cudaFuncSetAttribute(k_lu_inverse<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_lu_inverse<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        set_smem = smem;
+        set_smem[two] = smem;
     }
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel, &status};
-    return launch_cluster((const void*)k_lu_inverse, nel * GJ_CL, GJ_THREADS, smem, s, args);
+    return launch_cluster(kern, nel * GJ_CL, GJ_THREADS, smem, s, args);
 }
 
 size_t elim_smem_bytes(int nmv, int cw) {

@@ -20,10 +20,7 @@ constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
 constexpr int GJ_THREADS = 512;
 constexpr int GJ_NB_WARPS = GJ_THREADS / 32;
 constexpr int PUB_PAR = GJ_NB_WARPS * GJ_NB;   // one parity of the slab LU's published panel rows
-#ifndef MRCM_PANEL_WARPS
-#define MRCM_PANEL_WARPS 8
-#endif
-constexpr int PANEL_WARPS = MRCM_PANEL_WARPS;   // warps that factor a panel
+constexpr int PUB_FLOATS = 2 * PUB_PAR;        // both parities
 // inverse columns solved together in phase 2: IfPtrs::xch (64 unless the
 // slab is too large for shared memory)
 
@@ -632,6 +629,63 @@ cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Slab inverse through a blocked LU factorisation with partial pivoting
 // (FP32, column-major np x np, in place in D, inverse written to Dinv).
+// X <- L11^-1 X (LOWER, unit diagonal) or U11^-1 X on the rows of one
+// diagonal block by substitution, for nb right-hand sides: T holds the
+// factored block (T[c2 * ldt + c] = entry (c, c2), b x b, b a multiple of 4),
+// the entry (c, jj) of X is X[c * rs + jj * cs].  Eight consecutive lanes
+// share a right-hand side, four rows each; the entry solved at each step is
+// passed within the eight by a shuffle, so no barrier is needed and every
+// thread reads and writes only its own rows (up to four passes of the block
+// for nb <= 256).  The diagonal of U is applied as a correctly rounded
+// reciprocal; a zero pivot (already flagged singular) is taken as 1e-30.
+template <bool LOWER>
+__device__ void diag_solve(const float* __restrict__ T, int ldt, float* X, int rs, int cs, int b, int nb) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+        const int w = threadIdx.x + k * blockDim.x;
+        if (w - lane >= 8 * nb) break;   // warp-uniform: the whole warp is past the last right-hand side
+        const bool own = w < 8 * nb;
+        const int g = w & 7, jj = w >> 3;
+        float x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = (own && 4 * g + e < b) ? X[(4 * g + e) * rs + jj * cs] : 0.f;
+        if (LOWER) {
+#pragma unroll
+            for (int c = 0; c < GJ_NB; ++c) {
+                if (c < b) {
+                    const float xc = __shfl_sync(0xffffffffu, x[c & 3], c >> 2, 8);
+                    const float4 t = *reinterpret_cast<const float4*>(T + c * ldt + 4 * g);
+                    if (4 * g + 0 > c) x[0] -= t.x * xc;
+                    if (4 * g + 1 > c) x[1] -= t.y * xc;
+                    if (4 * g + 2 > c) x[2] -= t.z * xc;
+                    if (4 * g + 3 > c) x[3] -= t.w * xc;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = GJ_NB - 1; c >= 0; --c) {
+                if (c < b) {
+                    float d = T[c * ldt + c];
+                    if (d == 0.f) d = 1e-30f;
+                    if (g == (c >> 2)) x[c & 3] *= __frcp_rn(d);
+                    const float xc = __shfl_sync(0xffffffffu, x[c & 3], c >> 2, 8);
+                    const float4 t = *reinterpret_cast<const float4*>(T + c * ldt + 4 * g);
+                    if (4 * g + 0 < c) x[0] -= t.x * xc;
+                    if (4 * g + 1 < c) x[1] -= t.y * xc;
+                    if (4 * g + 2 < c) x[2] -= t.z * xc;
+                    if (4 * g + 3 < c) x[3] -= t.w * xc;
+                }
+            }
+        }
+        if (own) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (4 * g + e < b) X[(4 * g + e) * rs + jj * cs] = x[e];
+        }
+    }
+}
+
 // Phase 1 (cluster-synchronised per panel of GJ_NB columns): every CTA of
 // the cluster factors the panel redundantly in shared memory and inverts its
 // unit-lower and upper diagonal blocks; the owner writes the panel and the
@@ -694,8 +748,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     int* ownc = piv + np;                      // ncmax
     int* qpos = ownc + ncmax;                  // np
     float* pub = reinterpret_cast<float*>(qpos + np);   // 2 x PUB_PAR candidate rows published per column
-    unsigned* pkey = reinterpret_cast<unsigned*>(pub + 2 * PUB_PAR);   // 2 x GJ_NB_WARPS pivot keys
-    unsigned* pidx = pkey + 2 * GJ_NB_WARPS;                              // and their rows
+    unsigned* pkey = reinterpret_cast<unsigned*>(pub + PUB_FLOATS);   // 2 x GJ_NB_WARPS pivot keys
     __shared__ int nown;
     __shared__ int aff[2 * GJ_NB];
     __shared__ int naff;
@@ -730,12 +783,14 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         // holds, so a row interchange is two integer updates.  The registers
         // rotate left after every column, so the pivot column is always x[0]
         // and the column loop stays one short body.  One barrier per column:
-        // before it each warp reduces its pivot candidate (|a| as an unsigned
-        // key, smallest logical row on ties) by redux and publishes that row;
-        // after it every warp picks the winner among the warps' keys.  The
-        // published rows are double-buffered by the column's parity.  Each
-        // step leaves column c of every slot in Ps; the slots are put into
-        // logical row order once the panel is done.
+        // before it each warp reduces its pivot candidate by one redux and
+        // publishes that row; after it every warp picks the winner among the
+        // warps' keys by one more.  A key is |a| with its 11 low mantissa
+        // bits replaced by 2047 - (logical row - r0): the largest magnitude
+        // to 2^-12 relative wins, the first row among equals (threshold
+        // partial pivoting).  The published rows are double-buffered by the
+        // column's parity.  Each step leaves column c of every slot in Ps;
+        // the slots are put into logical row order once the panel is done.
         {
             float x[RPT][GJ_NB];
             int lp[RPT];
@@ -750,35 +805,31 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             for (int c = 0; c < b; ++c) {
                 const int r0 = k0 + c, par = c & 1;
                 float* pb = pub + par * PUB_PAR;            // [warp][GJ_NB] candidate rows
-                unsigned key = 0u, kr = 0xffffffffu;
+                unsigned key = 0u;   // 0: no candidate; a candidate's key is at least 1024 (np <= 1024)
+                int ks = -1;
 #pragma unroll
                 for (int i = 0; i < RPT; ++i) {
                     if (lp[i] >= r0 && lp[i] < np) {
                         const float v = fabsf(x[i][0]);
-                        const unsigned kb = v == v ? __float_as_uint(v) : 0u;   // NaN never wins over a number
-                        if (kr == 0xffffffffu || kb > key || (kb == key && (unsigned)lp[i] < kr)) {
-                            key = kb;
-                            kr = (unsigned)lp[i];
-                        }
+                        const unsigned kb = ((v == v ? __float_as_uint(v) : 0u) & ~0x7ffu) | (0x7ffu - (unsigned)(lp[i] - r0));
+                        if (kb > key) { key = kb; ks = i; }
                     }
                 }
                 const unsigned m = __reduce_max_sync(0xffffffffu, key);
-                const unsigned wi = __reduce_min_sync(0xffffffffu, (kr != 0xffffffffu && key == m) ? kr : 0xffffffffu);
 #pragma unroll
                 for (int i = 0; i < RPT; ++i)
-                    if ((unsigned)lp[i] == wi) {
+                    if (ks == i && key == m) {
                         float4* dst = reinterpret_cast<float4*>(pb + warp * GJ_NB);
 #pragma unroll
                         for (int q4 = 0; q4 < GJ_NB / 4; ++q4)
                             dst[q4] = make_float4(x[i][4 * q4], x[i][4 * q4 + 1], x[i][4 * q4 + 2], x[i][4 * q4 + 3]);
                     }
-                if (lane == 0) { pkey[par * GJ_NB_WARPS + warp] = m; pidx[par * GJ_NB_WARPS + warp] = wi; }
+                if (lane == 0) pkey[par * GJ_NB_WARPS + warp] = m;
                 __syncthreads();
                 const unsigned km = lane < GJ_NB_WARPS ? pkey[par * GJ_NB_WARPS + lane] : 0u;
-                const unsigned ki = lane < GJ_NB_WARPS ? pidx[par * GJ_NB_WARPS + lane] : 0xffffffffu;
-                const unsigned bm = __reduce_max_sync(0xffffffffu, ki != 0xffffffffu ? km : 0u);
-                const unsigned p = __reduce_min_sync(0xffffffffu, (ki != 0xffffffffu && km == bm) ? ki : 0xffffffffu);
-                const unsigned wb = __ballot_sync(0xffffffffu, ki == p && p != 0xffffffffu);
+                const unsigned bm = __reduce_max_sync(0xffffffffu, km);
+                const unsigned p = (unsigned)r0 + 0x7ffu - (bm & 0x7ffu);
+                const unsigned wb = __ballot_sync(0xffffffffu, km == bm && bm != 0u);
                 if (wb == 0u) {
                     // no candidate anywhere (cannot happen while r0 < np): keep the order, flag it
                     singular = true;
@@ -789,7 +840,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
                     const float4* src = reinterpret_cast<const float4*>(pb + pw * GJ_NB);
                     float a = pb[pw * GJ_NB];
                     if (a == 0.f) { singular = true; a = 1e-30f; }
-                    const float ia = 1.f / a;
+                    const float ia = __frcp_rn(a);   // correctly rounded, equal to 1.f / a
 #pragma unroll
                     for (int i = 0; i < RPT; ++i) {
                         if ((unsigned)lp[i] == p) lp[i] = r0;
@@ -868,30 +919,19 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         if (q % GJ_CL == rank)
             for (int c = warp; c < b; c += nwarp)
                 for (int r = k0 + lane; r < np; r += 32) A[(size_t)(k0 + c) * np + r] = Ps[c * np + r];
-        // U12 = L11^-1 A12 on owned trailing columns, by substitution (one thread per column)
-        for (int jj = tid; jj < no; jj += nt) {
-            const int j = ownc[jj];
-            if (j < k0 + b) {
-                for (int c = 0; c < GJ_NB; ++c) Upy[c * ncmax + jj] = 0.f;
-                continue;
-            }
-            float* col = A + (size_t)j * np;
-            float x[GJ_NB];
-#pragma unroll
-            for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? col[k0 + c] : 0.f;
-#pragma unroll
-            for (int c = 0; c < GJ_NB; ++c)
-#pragma unroll
-                for (int c2 = c + 1; c2 < GJ_NB; ++c2)
-                    if (c2 < b) x[c2] -= Ps[c * np + k0 + c2] * x[c];
-#pragma unroll
-            for (int c = 0; c < GJ_NB; ++c)
-                if (c < b) {
-                    col[k0 + c] = x[c];
-                    Upy[c * ncmax + jj] = x[c];
-                }
+        // U12 = L11^-1 A12 on owned trailing columns (zero on the others): the
+        // block rows staged in Upy, solved with the unit L11, written back
+        for (int w = tid; w < GJ_NB * no; w += nt) {
+            const int jj = w % no, c = w / no, j = ownc[jj];
+            Upy[c * ncmax + jj] = (j >= k0 + b && c < b) ? A[(size_t)j * np + k0 + c] : 0.f;
         }
         __syncthreads();
+        diag_solve<true>(Ps + k0, np, Upy, ncmax, 1, b, no);
+        __syncthreads();
+        for (int w = tid; w < b * no; w += nt) {
+            const int jj = w % no, c = w / no, j = ownc[jj];
+            if (j >= k0 + b) A[(size_t)j * np + k0 + c] = Upy[c * ncmax + jj];
+        }
         // trailing update A22 -= L21 U12 over owned trailing columns
         const int r1 = k0 + b;
         if (r1 < np) {
@@ -957,20 +997,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             for (int c = warp; c < b; c += nwarp)
                 for (int r = k0 + lane; r < np; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
             __syncthreads();
-            for (int jj = tid; jj < nb; jj += nt) {
-                float* xc = Xs + jj * np;
-                float x[GJ_NB];
-#pragma unroll
-                for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? xc[k0 + c] : 0.f;
-#pragma unroll
-                for (int c = 0; c < GJ_NB; ++c)
-#pragma unroll
-                    for (int c2 = c + 1; c2 < GJ_NB; ++c2)
-                        if (c2 < b) x[c2] -= Ps[c * np + k0 + c2] * x[c];
-#pragma unroll
-                for (int c = 0; c < GJ_NB; ++c)
-                    if (c < b) xc[k0 + c] = x[c];
-            }
+            diag_solve<true>(Ps + k0, np, Xs + k0, 1, np, b, nb);
             __syncthreads();
             tile_update(Ps, Xs, np, k0, b, k0 + b, np, nb);
             __syncthreads();
@@ -983,23 +1010,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             for (int c = warp; c < b; c += nwarp)
                 for (int r = k0 + lane; r < k0 + b; r += 32) Ps[c * np + r] = __ldcg(&A[(size_t)(k0 + c) * np + r]);
             __syncthreads();
-            for (int jj = tid; jj < nb; jj += nt) {
-                float* xc = Xs + jj * np;
-                float x[GJ_NB];
-#pragma unroll
-                for (int c = 0; c < GJ_NB; ++c) x[c] = c < b ? xc[k0 + c] : 0.f;
-#pragma unroll
-                for (int c = GJ_NB - 1; c >= 0; --c)
-                    if (c < b) {
-                        x[c] = x[c] / Ps[c * np + k0 + c];
-#pragma unroll
-                        for (int c2 = 0; c2 < GJ_NB; ++c2)
-                            if (c2 < c) x[c2] -= Ps[c * np + k0 + c2] * x[c];
-                    }
-#pragma unroll
-                for (int c = 0; c < GJ_NB; ++c)
-                    if (c < b) xc[k0 + c] = x[c];
-            }
+            diag_solve<false>(Ps + k0, np, Xs + k0, 1, np, b, nb);
             __syncthreads();
             tile_update(Ps, Xs, np, k0, b, 0, k0, nb);
             __syncthreads();
@@ -1016,8 +1027,9 @@ size_t lu_smem(int np, int xch) {
     const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
     const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
     const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)xch * np);
-    return sizeof(float) * ((size_t)GJ_NB * np + xs + up + 2 * PUB_PAR) +
-           sizeof(int) * ((size_t)np + ncmax + np + 4 * GJ_NB_WARPS) + 16;
+    if (np > 2 * GJ_THREADS) return (size_t)-1;   // two panel rows per thread at most
+    return sizeof(float) * ((size_t)GJ_NB * np + xs + up + PUB_FLOATS) +
+           sizeof(int) * ((size_t)np + ncmax + np + 2 * GJ_NB_WARPS) + 16;
 }
 
 

@@ -352,9 +352,89 @@ __device__ int warp_solve(const Box& B, const Ops& O, const T* Sinv, const T* cy
 // the warps meet in red (double-buffered by line parity, so one barrier per
 // line), and every warp forms the next line's input in its own zw (32
 // entries per warp).  w: scaled right-hand side in, scaled solution out.
+// FP32 sweeps of a CTA-wide solve, by warp 0 alone (no block barrier per
+// line; one warp is limited by the latency of the line-to-line exchange,
+// a 4-warp split by its barrier): lane i owns row i of the line (b <= 32).
+// The local operator is symmetric, so every block of S^-1 is too, and lane
+// i reads row i of the block -- with b a multiple of 4, as b / 4 float4
+// loads issued before the line's input is ready; otherwise column i by
+// scalar loads.  The line input goes through z (32 entries, zero beyond b)
+// and comes back as float4 broadcasts; four accumulators.  The other warps
+// wait at the closing barrier.
+__device__ __forceinline__ float sline_row_dot(const float* __restrict__ S, const float* z, int b, int lane,
+                                               float4 (&s4)[8]) {
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (4 * q < b) {
+            const float4 zz = reinterpret_cast<const float4*>(z)[q];
+            a[0] += s4[q].x * zz.x;
+            a[1] += s4[q].y * zz.y;
+            a[2] += s4[q].z * zz.z;
+            a[3] += s4[q].w * zz.w;
+        }
+    return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+__device__ __forceinline__ void load_srow(float4 (&s4)[8], const float* __restrict__ S, int b, int lane) {
+    const float4* Sr = reinterpret_cast<const float4*>(S + (lane < b ? lane : 0) * b);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s4[q] = 4 * q < b ? Sr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float sline_col_dot(const float* __restrict__ S, const float* z, int b, int lane) {
+    float a0 = 0.f, a1 = 0.f;
+    if (lane < b) {
+        int k = 0;
+        for (; k + 1 < b; k += 2) {
+            a0 += S[k * b + lane] * z[k];
+            a1 += S[(k + 1) * b + lane] * z[k + 1];
+        }
+        if (k < b) a0 += S[k * b + lane] * z[k];
+    }
+    return a0 + a1;
+}
+
+__device__ void warp0_sweeps(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* z,
+                             int b, int nb) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const size_t bb = (size_t)b * b;
+        const bool rows = (b & 3) == 0;
+        float4 s4[8];
+        float cur = 0.f;
+        // forward: w_j <- S_j^-1 (w_j + cys_{j-1} w_{j-1})
+        for (int j = 0; j < nb; ++j) {
+            if (rows) load_srow(s4, Sinv + j * bb, b, lane);
+            float zj = 0.f;
+            if (lane < b) zj = w[j * b + lane] + (j > 0 ? cys[(j - 1) * b + lane] * cur : 0.f);
+            z[lane] = zj;
+            __syncwarp();
+            cur = rows ? sline_row_dot(Sinv + j * bb, z, b, lane, s4) : sline_col_dot(Sinv + j * bb, z, b, lane);
+            if (lane < b) w[j * b + lane] = cur;
+            __syncwarp();
+        }
+        // backward: w_j <- w_j + S_j^-1 cys_j w_{j+1}
+        for (int j = nb - 2; j >= 0; --j) {
+            if (rows) load_srow(s4, Sinv + j * bb, b, lane);
+            z[lane] = lane < b ? cys[j * b + lane] * cur : 0.f;
+            const float wf = lane < b ? w[j * b + lane] : 0.f;
+            __syncwarp();
+            cur = wf + (rows ? sline_row_dot(Sinv + j * bb, z, b, lane, s4) : sline_col_dot(Sinv + j * bb, z, b, lane));
+            if (lane < b) w[j * b + lane] = cur;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void cta_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys, T* w, T* zw, T* red, int b,
                            int nb) {
+    if constexpr (std::is_same<T, float>::value) {
+        warp0_sweeps(Sinv, cys, w, zw, b, nb);
+        return;
+    }
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5, nq = blockDim.x >> 5;
     const int kq = (b + nq - 1) / nq, ka = wq * kq, kb = min(b, ka + kq);
     T* z = zw + wq * 32;

@@ -20,6 +20,7 @@
 // launchers defined in the other translation units
 size_t local2d_smem(int prec, int nx, int ny, int nrhs, bool part);
 size_t smooth2d_smem(int prec, int nx, int ny);
+size_t spack_bytes(int prec, int nx, int ny);
 cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int bw,
                            size_t smem, cudaStream_t s);
 cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems,
@@ -453,7 +454,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         }
         if (bx > 32 || ix > 32)
             return fail(h, MRCM_ERR_UNSUPPORTED, "2D boxes wider than 32 cells along x are not supported");
-        fac_stride = std::max(fac_stride, ((size_t)bx * bx * by + 3) & ~size_t(3));  // 16-byte aligned slots
+        fac_stride = std::max(fac_stride, spack_bytes(prec, bx, by) / tsz);   // smoothing packs, 16-byte multiples
         dsc_stride = std::max(dsc_stride, (size_t)bx * by);
         auto add = [&](int type, int nx, int ny, int nrhs) {
             int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;

@@ -539,6 +539,35 @@ __device__ int cta_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// The smoothing pack of one 2D subdomain: everything the smoothing solves
+// need that does not change between smoothing steps, written once after the
+// factorisation in the byte layout the smoothing kernel's shared memory
+// starts with, so that one bulk copy stages it.  S^-1 blocks first (the
+// factor slot other kernels read), then the FP64 operator (diagonal, x / y
+// couplings, Jacobi scaling), the box-side transmissibilities and Robin
+// beta, the fixed part of the right-hand side (sources and physical
+// boundary data) and the scaled y couplings of the sweeps.  Every field
+// starts on 16 bytes; the total is a multiple of 16.
+struct SPack {
+    size_t cd, cx, cy, dsc, bT, bB, bst, cys, bytes;
+};
+
+__host__ __device__ inline SPack spack_layout(int nx, int ny, size_t tsz) {
+    SPack L;
+    const size_t n = (size_t)nx * ny, m = 2 * (size_t)(nx + ny);
+    size_t o = align16(tsz * n * nx);
+    L.cd = o;  o += align16(sizeof(double) * n);
+    L.cx = o;  o += align16(sizeof(double) * n);
+    L.cy = o;  o += align16(sizeof(double) * n);
+    L.dsc = o; o += align16(sizeof(double) * n);
+    L.bT = o;  o += align16(sizeof(double) * m);
+    L.bB = o;  o += align16(sizeof(double) * m);
+    L.bst = o; o += align16(sizeof(double) * n);
+    L.cys = o; o += align16(tsz * n);
+    L.bytes = o;
+    return L;
+}
+
 // Shared-memory carve-up ----------------------------------------------------
 template <typename T>
 struct Carve {

@@ -47,14 +47,30 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
     fill_scale(B, C.O, mixed);
     factor_box<T, BW>(B, C.O, C.Sinv, C.cys, C.cxs, C.Sbuf, &C.flags[0]);
 
-    // keep the factor for the smoothing steps
+    // keep the factor for the smoothing steps, as the subdomain's smoothing pack
     const bool keep = (job.type == JOB_SFACT) || (job.type == JOB_BASIS && Mth.same_alpha);
     if (keep) {
-        T* dst = (T*)P.fac + (size_t)job.item * P.fac_stride;
+        unsigned char* pk = (unsigned char*)((T*)P.fac + (size_t)job.item * P.fac_stride);
+        const SPack L = spack_layout(B.nx, B.ny, sizeof(T));
+        T* dst = (T*)pk;
         const size_t nS = (size_t)B.n * B.nx;
         for (size_t t = threadIdx.x; t < nS; t += blockDim.x) dst[t] = C.Sinv[t];
         double* dd = P.dsc + (size_t)job.item * P.dsc_stride;
-        for (int c = threadIdx.x; c < B.n; c += blockDim.x) dd[c] = C.O.dsc[c];
+        const double* fk = P.f + md.cell_off;
+        const double vk = md.h[0] * md.h[1];
+        for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
+            dd[c] = C.O.dsc[c];
+            ((double*)(pk + L.cd))[c] = C.O.cd[c];
+            ((double*)(pk + L.cx))[c] = C.O.cx[c];
+            ((double*)(pk + L.cy))[c] = C.O.cy[c];
+            ((double*)(pk + L.dsc))[c] = C.O.dsc[c];
+            ((double*)(pk + L.bst))[c] = source_rhs(B, C.O, fk, md.n[0], vk, md.h[1], md.h[0], nullptr, c % B.nx, c / B.nx);
+            ((T*)(pk + L.cys))[c] = C.cys[c];
+        }
+        for (int t = threadIdx.x; t < 2 * (B.nx + B.ny); t += blockDim.x) {
+            ((double*)(pk + L.bT))[t] = C.O.bT[t];
+            ((double*)(pk + L.bB))[t] = C.O.bB[t];
+        }
     }
     if (C.flags[0] && threadIdx.x == 0) {
         atomicOr(&P.status[0], ST_NOT_SPD);
@@ -198,47 +214,44 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     if (threadIdx.x == 0) setup_box(B, md, sd.loh, sd.hih, Mth.alpha_s);
     __syncthreads();
     const size_t n = (size_t)B.n;
-    size_t o = 0;
-    auto take = [&](size_t bytes) { unsigned char* p = smem + o; o += align16(bytes); return p; };
-    T* Sinv = (T*)take(sizeof(T) * n * B.nx);
+    // the smoothing pack (factor, operator, fixed right-hand side) first, by one bulk copy
+    const SPack L = spack_layout(B.nx, B.ny, sizeof(T));
+    T* Sinv = (T*)smem;
     Ops O;
-    O.cd = (double*)take(sizeof(double) * n);
-    O.cx = (double*)take(sizeof(double) * n);
-    O.cy = (double*)take(sizeof(double) * n);
-    O.dsc = (double*)take(sizeof(double) * n);
-    O.hk = (double*)take(sizeof(double) * 2 * n);
-    O.bT = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
-    O.bB = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
+    O.cd = (double*)(smem + L.cd);
+    O.cx = (double*)(smem + L.cx);
+    O.cy = (double*)(smem + L.cy);
+    O.dsc = (double*)(smem + L.dsc);
+    O.hk = nullptr;
+    O.bT = (double*)(smem + L.bT);
+    O.bB = (double*)(smem + L.bB);
+    double* bsrc = (double*)(smem + L.bst);   // fixed part, then the Robin terms of this step
+    T* cys = (T*)(smem + L.cys);
+    size_t o = L.bytes;
+    auto take = [&](size_t bytes) { unsigned char* p = smem + o; o += align16(bytes); return p; };
     double* lam = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
-    double* bsrc = (double*)take(sizeof(double) * n);
-    T* cys = (T*)take(sizeof(T) * n);
-    T* zbuf = (T*)take(sizeof(T) * 32 * SM_WARPS);       // one line input per warp
-    T* red = (T*)take(sizeof(T) * 2 * 32 * SM_WARPS);    // partial sums of the warps, two line parities
+    double* lun = (double*)take(sizeof(double) * 2 * (B.nx + B.ny));
+    T* zbuf = (T*)take(sizeof(T) * 32 * SM_WARPS);       // line input of the sweeps
+    T* red = (T*)take(sizeof(T) * 2 * 32 * SM_WARPS);    // partial sums of the warps (FP64 sweeps), two line parities
     unsigned int* nrm = (unsigned int*)take(16);
     double* x = (double*)take(sizeof(double) * n);
     T* w = mixed ? (T*)take(sizeof(T) * n) : (T*)x;
     int* flags = (int*)take(64);
-    // the bulk copy moves a multiple of 16 bytes; the factor stride and the
-    // shared-memory slot are padded to 16 bytes
-    const uint32_t sbytes = (uint32_t)((sizeof(T) * n * B.nx + 15) & ~size_t(15));
-    const T* Sg = (const T*)P.fac + (size_t)item * P.fac_stride;
+    const uint32_t pbytes = (uint32_t)L.bytes;
+    const unsigned char* Pg = (const unsigned char*)((const T*)P.fac + (size_t)item * P.fac_stride);
     if (threadIdx.x == 0) {
         flags[0] = 0;
         flags[1] = 0;
         mbar_init(&bar, 1);
-        mbar_expect_tx(&bar, sbytes);
-        bulk_g2s(Sinv, Sg, sbytes, &bar);
+        mbar_expect_tx(&bar, pbytes);
+        bulk_g2s(smem, Pg, pbytes, &bar);
     }
-    build_ops(B, md, P, O);
-    const double* dd = P.dsc + (size_t)item * P.dsc_stride;
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x) O.dsc[c] = dd[c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x)
-        cys[c] = (T)(O.cy[c] * O.dsc[c] * ((c + B.nx < B.n) ? O.dsc[c + B.nx] : 0.0));
-    // Robin data from the current solution: lambda = -beta u.n + pi with n the
-    // outward normal of hat-Omega_i and pi = p - u.n h / (2K) of the cell inside.
+    // Robin data from the current solution, while the pack is in flight:
+    // lambda = -beta u.n + pi with n the outward normal of hat-Omega_i and
+    // pi = p - u.n h / (2K) of the cell inside
     const double* pst = P.p + md.cell_off;
     const double* ust = P.u + md.cell_off * 4;
+    const double* hkg = P.hk + md.cell_off * 3;
     for (int sid = 0; sid < 4; ++sid) {
         if (B.kind[sid] != 2) continue;
         const int a = sid >> 1;
@@ -249,22 +262,33 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
             else        { i = pos; j = (sid == 2) ? 0 : B.ny - 1; }
             const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
             const double un = ust[g * 4 + sid];
-            const double pi = pst[g] - un * O.hk[2 * (j * B.nx + i) + a];
-            lam[side_off(B, sid) + pos] = -O.bB[side_off(B, sid) + pos] * un + pi;
+            lun[side_off(B, sid) + pos] = un;
+            lam[side_off(B, sid) + pos] = pst[g] - un * hkg[g * 3 + a];
         }
     }
-    __syncthreads();
-    const double vol = md.h[0] * md.h[1];
-    const double* fm = P.f + md.cell_off;
-    for (int c = threadIdx.x; c < B.n; c += blockDim.x) {
-        const int i = c % B.nx, j = c / B.nx;
-        bsrc[c] = source_rhs(B, O, fm, md.n[0], vol, md.h[1], md.h[0], lam, i, j);
-    }
-    __syncthreads();
     int it = 0;
-    // every thread reads the staged factor: all wait for the copy, and agree on a late one
+    // every thread reads the staged pack: all wait for the copy, and agree on a late one
     const bool arrived = mbar_wait(&bar, 0);
     if (!__syncthreads_or(!arrived)) {
+        for (int sid = 0; sid < 4; ++sid) {
+            if (B.kind[sid] != 2) continue;
+            const int len = (sid >> 1) == 0 ? B.ny : B.nx;
+            for (int pos = threadIdx.x; pos < len; pos += blockDim.x)
+                lam[side_off(B, sid) + pos] -= O.bB[side_off(B, sid) + pos] * lun[side_off(B, sid) + pos];
+        }
+        __syncthreads();
+        // Robin terms of the right-hand side, one side at a time (corner cells lie on two)
+        for (int sid = 0; sid < 4; ++sid) {
+            if (B.kind[sid] != 2) continue;
+            const int a = sid >> 1;
+            const int len = a == 0 ? B.ny : B.nx;
+            for (int pos = threadIdx.x; pos < len; pos += blockDim.x) {
+                const int i = a == 0 ? ((sid == 0) ? 0 : B.nx - 1) : pos;
+                const int j = a == 0 ? pos : ((sid == 2) ? 0 : B.ny - 1);
+                bsrc[j * B.nx + i] += O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos];
+            }
+            __syncthreads();
+        }
         RhsStored rs{bsrc};
         it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
     } else if (threadIdx.x == 0) {
@@ -327,13 +351,16 @@ size_t local2d_smem(int prec, int nx, int ny, int nrhs, bool part) {
     return prec == 0 ? carve_bytes<double>(nx, ny, nrhs, part) : carve_bytes<float>(nx, ny, nrhs, part);
 }
 
+size_t spack_bytes(int prec, int nx, int ny) {
+    return spack_layout(nx, ny, prec == 0 ? sizeof(double) : sizeof(float)).bytes;
+}
+
 size_t smooth2d_smem(int prec, int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
-    size_t s = align16(tsz * n * nx);
-    s += align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);
-    s += align16(sizeof(double) * 2 * (nx + ny)) * 3 + align16(sizeof(double) * n);
-    s += align16(tsz * n) + align16(tsz * 32 * SM_WARPS) + align16(tsz * 2 * 32 * SM_WARPS) + 16;
+    size_t s = spack_bytes(prec, nx, ny);
+    s += align16(sizeof(double) * 2 * (nx + ny)) * 2;
+    s += align16(tsz * 32 * SM_WARPS) + align16(tsz * 2 * 32 * SM_WARPS) + 16;
     s += align16(sizeof(double) * n);
     if (prec != 0) s += align16(tsz * n);
     return s + 64;

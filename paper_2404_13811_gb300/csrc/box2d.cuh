@@ -487,10 +487,14 @@ __device__ void cta_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys
 
 // One right-hand side solved by the whole CTA (as warp_solve: FP64 form one
 // solve; mixed form FP32 sweeps + FP64 residual refinement, residual and
-// norms over all threads).  nrm: 2 unsigned ints of shared memory.
+// norms over all threads).  nrm: 2 unsigned ints of shared memory.  warm
+// (mixed form): x holds a starting iterate on entry and the refinement
+// starts from its residual; the stopping rule stays relative to the
+// right-hand side, so the result meets the same tolerance, and no sweep is
+// run when the start already does.
 template <typename T, typename Rhs>
 __device__ int cta_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys, double* x, T* w, T* zw, T* red,
-                         unsigned int* nrm, const Rhs& rhs, double tol, int max_ir, int* noconv) {
+                         unsigned int* nrm, const Rhs& rhs, double tol, int max_ir, int* noconv, bool warm = false) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int b = B.nx, nb = B.ny;
     if (std::is_same<T, double>::value) {
@@ -501,18 +505,31 @@ __device__ int cta_solve(const Box& B, const Ops& O, const T* Sinv, const T* cys
     }
     if (tid < 2) nrm[tid] = 0u;
     __syncthreads();
-    float bn = 0.f;
+    float bn = 0.f, r0 = 0.f;
     for (int c = tid; c < B.n; c += nt) {
-        const T wc = (T)(O.dsc[c] * rhs(B, O, c % b, c / b));
-        x[c] = 0.0;
+        const int i = c % b, j = c / b;
+        const double bc = rhs(B, O, i, j);
+        const T wc = (T)(O.dsc[c] * (warm ? bc - apply_A(B, O, x, i, j) : bc));
         w[c] = wc;
-        bn = fmaxf(bn, fabsf((float)wc));
+        bn = fmaxf(bn, fabsf((float)(O.dsc[c] * bc)));
+        r0 = fmaxf(r0, fabsf((float)wc));
     }
-    for (int o = 16; o; o >>= 1) bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
-    if ((tid & 31) == 0) atomicMax(&nrm[0], __float_as_uint(bn));
+    if (!warm)
+        for (int c = tid; c < B.n; c += nt) x[c] = 0.0;
+    for (int o = 16; o; o >>= 1) {
+        bn = fmaxf(bn, __shfl_xor_sync(0xffffffffu, bn, o));
+        r0 = fmaxf(r0, __shfl_xor_sync(0xffffffffu, r0, o));
+    }
+    if ((tid & 31) == 0) {
+        atomicMax(&nrm[0], __float_as_uint(bn));
+        atomicMax(&nrm[1], __float_as_uint(r0));
+    }
     __syncthreads();
     bn = __uint_as_float(nrm[0]);
+    r0 = __uint_as_float(nrm[1]);
+    __syncthreads();   // nrm[1] is reset at the top of the first step
     int it = 0;
+    if (warm && ((double)r0 <= tol * (double)bn || bn == 0.f)) return 0;
     for (; it < max_ir; ++it) {
         cta_sweeps<T>(Sinv, cys, w, zw, red, b, nb);
         for (int c = tid; c < B.n; c += nt) x[c] += O.dsc[c] * (double)w[c];

@@ -266,6 +266,10 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
             lam[side_off(B, sid) + pos] = pst[g] - un * hkg[g * 3 + a];
         }
     }
+    // mixed form: the refinement starts from the current pressure on the box
+    if (mixed)
+        for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+            x[c] = pst[(B.lo[0] + c % B.nx) + (long long)md.n[0] * (B.lo[1] + c / B.nx)];
     int it = 0;
     // every thread reads the staged pack: all wait for the copy, and agree on a late one
     const bool arrived = mbar_wait(&bar, 0);
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
             __syncthreads();
         }
         RhsStored rs{bsrc};
-        it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0]);
+        it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0], mixed);
     } else if (threadIdx.x == 0) {
         flags[1] = 1;
     }

@@ -333,43 +333,64 @@ __device__ __forceinline__ float warp_dot(const float* row, const float* v, int 
     return acc;
 }
 
-// forward: y_j = Dinv_j b_j (stored in place), then push into the neighbours
-__global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float fsm[];
-    const int e = blockIdx.x;
-    if (e >= nel) return;
+// The sweeps of the reduction: one cluster of SW_CL CTAs per slab, so that
+// the products with the slab inverse (n x n FP32, read from L2 / HBM) have
+// SW_CL times the loads in flight of a single CTA.  Partial products over
+// column chunks are summed through distributed shared memory in a fixed
+// order (the result does not depend on timing).
+constexpr int SW_CL = 8;
+constexpr int SW_T = 256;
+
+// forward: y_j = Dinv_j b_j (stored in place), then push into the neighbours:
+// b_jm[mrows] -= Rup y_j, b_jp[vrows] -= Rdn y_j.
+__global__ void __launch_bounds__(SW_T) k_bcr_fwd(IfPtrs I, const ElimDev* el, int nel) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / SW_CL;   // the grid is nel clusters
+    extern __shared__ __align__(16) float fsm[];
+    const int np = I.npad;
+    float* part = fsm;        // np: Dinv_j b_j over this CTA's column chunk
+    float* y = fsm + np;      // np: y_j
+    float* bs = y + np;       // the column chunk of b_j
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, nwarp = nt >> 5;
     const ElimDev E = el[e];
     const SlabDev Sj = I.slabs[E.j];
-    const int np = I.npad;
+    const int n = Sj.n;
+    const int cw = (n + SW_CL - 1) / SW_CL, c0 = min(n, rank * cw), c1 = min(n, c0 + cw);
     const float* Dinv = I.Dinv + Sj.offD;
     float* bj = I.bq + Sj.col0;
-    float* bs = fsm;            // n_j
-    float* y = fsm + np;        // n_j
-    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bs[r] = bj[r];
+    for (int c = c0 + tid; c < c1; c += nt) bs[c - c0] = bj[c];
     __syncthreads();
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
+    for (int r = tid; r < n; r += nt) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int c = 0;
-        for (; c + 3 < Sj.n; c += 4) {
-            a0 += Dinv[(size_t)c * np + r] * bs[c];
-            a1 += Dinv[(size_t)(c + 1) * np + r] * bs[c + 1];
-            a2 += Dinv[(size_t)(c + 2) * np + r] * bs[c + 2];
-            a3 += Dinv[(size_t)(c + 3) * np + r] * bs[c + 3];
+        int c = c0;
+        for (; c + 3 < c1; c += 4) {
+            a0 += Dinv[(size_t)c * np + r] * bs[c - c0];
+            a1 += Dinv[(size_t)(c + 1) * np + r] * bs[c + 1 - c0];
+            a2 += Dinv[(size_t)(c + 2) * np + r] * bs[c + 2 - c0];
+            a3 += Dinv[(size_t)(c + 3) * np + r] * bs[c + 3 - c0];
         }
-        for (; c < Sj.n; ++c) a0 += Dinv[(size_t)c * np + r] * bs[c];
-        y[r] = (a0 + a1) + (a2 + a3);
+        for (; c < c1; ++c) a0 += Dinv[(size_t)c * np + r] * bs[c - c0];
+        part[r] = (a0 + a1) + (a2 + a3);
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bj[r] = y[r];
+    cluster.sync();   // partials complete; every chunk of b_j read before it is overwritten
+    for (int r = tid; r < n; r += nt) {
+        float acc = 0.f;
+        for (int q = 0; q < SW_CL; ++q) acc += cluster.map_shared_rank(part, q)[r];
+        y[r] = acc;
+    }
+    cluster.sync();   // no CTA leaves while its partials may still be read
+    if (rank == 0)
+        for (int r = tid; r < n; r += nt) bj[r] = y[r];
     if (E.jm >= 0 && E.jm != E.j) {
         const SlabDev Sm = I.slabs[E.jm];
         const float* Rup = I.Rup + Sj.offRup;
         const int* mrows_m = I.idx + Sm.offIdx;
         float* bm = I.bq + Sm.col0;
-        for (int r = warp; r < Sm.nm; r += nwarp) {
-            const float acc = warp_dot(Rup + (size_t)r * Sj.n, y, Sj.n);
-            if ((threadIdx.x & 31) == 0) bm[mrows_m[r]] -= acc;
+        for (int r = rank * nwarp + warp; r < Sm.nm; r += SW_CL * nwarp) {
+            const float acc = warp_dot(Rup + (size_t)r * n, y, n);
+            if ((tid & 31) == 0) bm[mrows_m[r]] -= acc;
         }
     }
     if (E.jp >= 0) {
@@ -377,56 +398,84 @@ __global__ void __launch_bounds__(256) k_bcr_fwd(IfPtrs I, const ElimDev* el, in
         const float* Rdn = I.Rdn + Sj.offRdn;
         const int* vrows_p = I.idx + Sp.offIdx + Sp.nm;
         float* bp = I.bq + Sp.col0;
-        for (int r = warp; r < Sp.nv; r += nwarp) {
-            const float acc = warp_dot(Rdn + (size_t)r * Sj.n, y, Sj.n);
-            if ((threadIdx.x & 31) == 0) bp[vrows_p[r]] -= acc;
+        for (int r = rank * nwarp + warp; r < Sp.nv; r += SW_CL * nwarp) {
+            const float acc = warp_dot(Rdn + (size_t)r * n, y, n);
+            if ((tid & 31) == 0) bp[vrows_p[r]] -= acc;
         }
     }
 }
 
-// backward: x_j = y_j - Qv (Cdn_j x_jm) - Qm (Cup_j x_jp)
-__global__ void __launch_bounds__(256) k_bcr_bwd(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float bsm[];
-    const int e = blockIdx.x;
-    if (e >= nel) return;
+// backward: x_j = y_j - Dinv_j[:, vrows] (Cdn_j x_jm) - Dinv_j[:, mrows] (Cup_j x_jp).
+// The coupling products are split over the cluster by rows (contiguous
+// chunks, gathered through distributed shared memory), the products with
+// the inverse columns by chunks of those columns, the final sum by rows.
+__global__ void __launch_bounds__(SW_T) k_bcr_bwd(IfPtrs I, const ElimDev* el, int nel) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / SW_CL;
+    extern __shared__ __align__(16) float bsm[];
+    const int np = I.npad;
+    float* xm = bsm;              // n_jm
+    float* xp = bsm + np;         // n_jp
+    float* tl = bsm + 2 * np;     // this CTA's entries of (tv, tm), at their own positions
+    float* tv = bsm + 3 * np;     // nv_j
+    float* tm = bsm + 4 * np;     // nm_j
+    float* part = bsm + 5 * np;   // np
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, nwarp = nt >> 5;
     const ElimDev E = el[e];
     const SlabDev Sj = I.slabs[E.j];
-    const int np = I.npad;
+    const int n = Sj.n;
     const float* Dinv = I.Dinv + Sj.offD;
     const int* mrows_j = I.idx + Sj.offIdx;
     const int* vrows_j = mrows_j + Sj.nm;
-    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    float* xm = bsm;              // n_jm
-    float* xp = bsm + np;         // n_jp
-    float* tv = bsm + 2 * np;     // nv_j
-    float* tm = tv + np;          // nm_j
     const SlabDev Sm = I.slabs[E.jm];
-    for (int c = threadIdx.x; c < Sm.n; c += blockDim.x) xm[c] = I.bq[Sm.col0 + c];
-    const int nmj = E.jp >= 0 ? Sj.nm : 0;
+    for (int c = tid; c < Sm.n; c += nt) xm[c] = I.bq[Sm.col0 + c];
+    const int nv = Sj.nv, nmj = E.jp >= 0 ? Sj.nm : 0, nq = nv + nmj;
     SlabDev Sp{};
     if (E.jp >= 0) {
         Sp = I.slabs[E.jp];
-        for (int c = threadIdx.x; c < Sp.n; c += blockDim.x) xp[c] = I.bq[Sp.col0 + c];
+        for (int c = tid; c < Sp.n; c += nt) xp[c] = I.bq[Sp.col0 + c];
     }
     __syncthreads();
+    // (tv, tm) entries q in [k0, k1) of the nq coupling rows (tv first)
+    const int kw = (nq + SW_CL - 1) / SW_CL, k0 = min(nq, rank * kw), k1 = min(nq, k0 + kw);
     const float* Cdn_j = I.Cdn + Sj.offCdn;
     const float* Cup_j = I.Cup + Sj.offCup;
-    for (int q = warp; q < Sj.nv; q += nwarp) {
-        const float acc = warp_dot(Cdn_j + (size_t)q * Sj.ldc, xm, Sm.n);
-        if ((threadIdx.x & 31) == 0) tv[q] = acc;
+    for (int q = k0 + warp; q < k1; q += nwarp) {
+        const float acc = q < nv ? warp_dot(Cdn_j + (size_t)q * Sj.ldc, xm, Sm.n)
+                                 : warp_dot(Cup_j + (size_t)(q - nv) * Sj.ldc, xp, Sp.n);
+        if ((tid & 31) == 0) tl[q] = acc;
     }
-    for (int q = warp; q < nmj; q += nwarp) {
-        const float acc = warp_dot(Cup_j + (size_t)q * Sj.ldc, xp, Sp.n);
-        if ((threadIdx.x & 31) == 0) tm[q] = acc;
+    cluster.sync();
+    for (int q = tid; q < nq; q += nt) {
+        const float v = cluster.map_shared_rank(tl, q / kw)[q];
+        if (q < nv) tv[q] = v;
+        else tm[q - nv] = v;
     }
     __syncthreads();
-    float* xj = I.bq + Sj.col0;
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
-        float acc = xj[r];
-        for (int q = 0; q < Sj.nv; ++q) acc -= Dinv[(size_t)vrows_j[q] * np + r] * tv[q];
-        for (int q = 0; q < nmj; ++q) acc -= Dinv[(size_t)mrows_j[q] * np + r] * tm[q];
-        xj[r] = acc;
+    // partial products over this CTA's chunk of the coupling columns
+    for (int r = tid; r < n; r += nt) {
+        float a0 = 0.f, a1 = 0.f;
+        int q = k0;
+        for (; q + 1 < k1; q += 2) {
+            const int ca = q < nv ? vrows_j[q] : mrows_j[q - nv];
+            const int cb = q + 1 < nv ? vrows_j[q + 1] : mrows_j[q + 1 - nv];
+            a0 += Dinv[(size_t)ca * np + r] * (q < nv ? tv[q] : tm[q - nv]);
+            a1 += Dinv[(size_t)cb * np + r] * (q + 1 < nv ? tv[q + 1] : tm[q + 1 - nv]);
+        }
+        if (q < k1) a0 += Dinv[(size_t)(q < nv ? vrows_j[q] : mrows_j[q - nv]) * np + r] * (q < nv ? tv[q] : tm[q - nv]);
+        part[r] = a0 + a1;
     }
+    cluster.sync();
+    const int rw = (n + SW_CL - 1) / SW_CL, r0 = min(n, rank * rw), r1 = min(n, r0 + rw);
+    float* xj = I.bq + Sj.col0;
+    for (int r = r0 + tid; r < r1; r += nt) {
+        float acc = 0.f;
+        for (int q = 0; q < SW_CL; ++q) acc += cluster.map_shared_rank(part, q)[r];
+        xj[r] -= acc;
+    }
+    cluster.sync();   // no CTA leaves while its shared memory may still be read
 }
 
 __global__ void k_if_update(IfPtrs I, int ncols) {
@@ -609,16 +658,37 @@ cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int f
     return cudaGetLastError();
 }
 
+static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
+                                  void** args, int cl = GJ_CL) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_fwd<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel};
+    const size_t smem = sizeof(float) * (2 * (size_t)nmax + (nmax + SW_CL - 1) / SW_CL);
+    return launch_cluster((const void*)k_bcr_fwd, nel * SW_CL, SW_T, smem, s, args, SW_CL);
 }
 
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_bwd<<<nel, 256, sizeof(float) * 4 * nmax, s>>>(I, el, nel);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel};
+    const size_t smem = sizeof(float) * 6 * (size_t)nmax;
+    return launch_cluster((const void*)k_bcr_bwd, nel * SW_CL, SW_T, smem, s, args, SW_CL);
 }
 
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
@@ -1032,23 +1102,6 @@ size_t lu_smem(int np, int xch) {
            sizeof(int) * ((size_t)np + ncmax + np + 2 * GJ_NB_WARPS) + 16;
 }
 
-
-static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
-                                  void** args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nblocks);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = GJ_CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, kern, args);
-}
 
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;

@@ -161,57 +161,97 @@ __global__ void k_bcr_fill(IfPtrs I, int nslab) {
 // where Qv / Qm are the columns of Dinv_j at j's pressure / flux coupling
 // rows, Rup = Cup_jm (saved) and Rdn = Cdn_jp (saved).
 // ---------------------------------------------------------------------------
-// Rows x Q product: out[m][n] = sum_k L[m][k] Dinv[k][col(n)] for m < M, n < N,
-// with L row-major (ld n_j) in global memory and the columns of Dinv picked
-// by `cols`.  K is staged through shared memory in chunks of 32.
+// AT <- (L Q)^T with L (M x K, row-major in global memory) and Q the
+// columns cols[0..N) of Dinv (rows 0..K): AT[n * Mp + m], Mp / Np = M / N
+// rounded up to 4, zero beyond M / N.  K in chunks of 32 staged transposed
+// (stLT[k * (Mp + 4) + m], stQ[k * (Np + 4) + n]); every thread owns 4 x 4
+// output tiles, read as float4 pairs per k (16 FMAs per two loads).  The
+// sum over k runs in increasing k for every entry.
 __device__ void rows_times_cols(const float* L, int M, int K, const float* Dinv, int np, const int* cols, int N,
-                                float* out, float* stL, float* stQ) {
+                                float* AT, float* stLT, float* stQ) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < M * N; t += nt) out[t] = 0.f;
+    const int Mp = (M + 3) & ~3, Np = (N + 3) & ~3, ldl = Mp + 4, ldq = Np + 4;
+    const int tm = Mp >> 2, tn = Np >> 2;
+    for (int t = tid; t < Np * Mp; t += nt) AT[t] = 0.f;
     for (int k0 = 0; k0 < K; k0 += 32) {
         const int kb = min(32, K - k0);
         __syncthreads();
-        for (int t = tid; t < M * 32; t += nt) {
+        for (int t = tid; t < Mp * 32; t += nt) {
             const int m = t >> 5, k = t & 31;
-            stL[t] = k < kb ? __ldcg(&L[(size_t)m * K + k0 + k]) : 0.f;
+            stLT[k * ldl + m] = (k < kb && m < M) ? __ldcg(&L[(size_t)m * K + k0 + k]) : 0.f;
         }
-        for (int t = tid; t < N * 32; t += nt) {
+        for (int t = tid; t < Np * 32; t += nt) {
             const int n = t >> 5, k = t & 31;
-            stQ[k * N + n] = k < kb ? Dinv[(size_t)cols[n] * np + k0 + k] : 0.f;
+            stQ[k * ldq + n] = (k < kb && n < N) ? Dinv[(size_t)cols[n] * np + k0 + k] : 0.f;
         }
         __syncthreads();
-        for (int t = tid; t < M * N; t += nt) {
-            const int m = t / N, n = t - (t / N) * N;
-            float acc = out[t];
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) acc += stL[m * 32 + k] * stQ[k * N + n];
-            out[t] = acc;
+        for (int t = tid; t < tm * tn; t += nt) {
+            const int i = t / tn, jn = t - (t / tn) * tn;
+            float acc[4][4];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const float4 v = *reinterpret_cast<const float4*>(&AT[(4 * jn + y) * Mp + 4 * i]);
+                acc[0][y] = v.x; acc[1][y] = v.y; acc[2][y] = v.z; acc[3][y] = v.w;
+            }
+            for (int k = 0; k < kb; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(&stLT[k * ldl + 4 * i]);
+                const float4 q = *reinterpret_cast<const float4*>(&stQ[k * ldq + 4 * jn]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * qv[y];
+            }
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+                *reinterpret_cast<float4*>(&AT[(4 * jn + y) * Mp + 4 * i]) = make_float4(acc[0][y], acc[1][y], acc[2][y], acc[3][y]);
         }
     }
     __syncthreads();
 }
 
-// out rows r of a target: tgt(r, c) op= sum_q A[r][q] C[q][c] for c < ncol,
-// with C row-major (ld ldc) in global memory staged in shared memory.
+// Rows r < M of a target: tgt(r, c) op= sum_q A[r][q] C[q][c] for c < ncol,
+// with A given transposed (AT[q * Mp + r], q < Np = M2 rounded up to 4,
+// zero-padded) and C row-major (ld ldc) in global memory, staged in shared
+// memory in column chunks of at most cwmax (Csm[q * cwp + c]).  4 x 4
+// register tiles as above; the sum over q runs in increasing q.
 template <bool ACCUM_INTO_D>
-__device__ void apply_coupling(const float* Asm, int M, int M2, const float* Cg, int ldc, int ncol, float* Csm,
+__device__ void apply_coupling(const float* AT, int M, int M2, const float* Cg, int ldc, int ncol, float* Csm,
                                int cwmax, float* D, int np, const int* rows, float* Cout, int ldout, int nclear) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    // columns in chunks of at most cwmax (the staged block is M2 x cw)
+    const int Mp = (M + 3) & ~3, Np = (M2 + 3) & ~3, tm = Mp >> 2;
     for (int c0 = 0; c0 < ncol; c0 += cwmax) {
-        const int cw = min(cwmax, ncol - c0);
+        const int cw = min(cwmax, ncol - c0), cwp = (cw + 3) & ~3, tc = cwp >> 2;
         __syncthreads();
-        for (int t = tid; t < M2 * cw; t += nt) {
-            const int q = t / cw, c = t - (t / cw) * cw;
-            Csm[t] = Cg[(size_t)q * ldc + c0 + c];
+        for (int t = tid; t < Np * cwp; t += nt) {
+            const int q = t / cwp, c = t - (t / cwp) * cwp;
+            Csm[t] = (q < M2 && c < cw) ? Cg[(size_t)q * ldc + c0 + c] : 0.f;
         }
         __syncthreads();
-        for (int t = tid; t < M * cw; t += nt) {
-            const int r = t / cw, c = t - (t / cw) * cw;
-            float acc = 0.f;
-            for (int q = 0; q < M2; ++q) acc += Asm[r * M2 + q] * Csm[q * cw + c];
-            if (ACCUM_INTO_D) D[(size_t)(c0 + c) * np + rows[r]] -= acc;
-            else Cout[(size_t)r * ldout + c0 + c] = -acc;
+        for (int t = tid; t < tm * tc; t += nt) {
+            const int i = t / tc, jc = t - (t / tc) * tc;
+            float acc[4][4] = {};
+            for (int q = 0; q < M2; ++q) {
+                const float4 a = *reinterpret_cast<const float4*>(&AT[q * Mp + 4 * i]);
+                const float4 cc = *reinterpret_cast<const float4*>(&Csm[q * cwp + 4 * jc]);
+                const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * cv[y];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int r = 4 * i + x;
+                if (r >= M) continue;
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int c = 4 * jc + y;
+                    if (c >= cw) continue;
+                    if (ACCUM_INTO_D) D[(size_t)(c0 + c) * np + rows[r]] -= acc[x][y];
+                    else Cout[(size_t)r * ldout + c0 + c] = -acc[x][y];
+                }
+            }
         }
     }
     if (!ACCUM_INTO_D)
@@ -284,10 +324,11 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
         for (int t = tid; t < Sm.nm * Sm.ldc; t += nt) CupM[t] = 0.f;
         return;
     }
-    float* Asm = esm;                   // M x N
-    float* stL = Asm + M * N;           // M x 32
-    float* stQ = stL + M * 32;          // 32 x N
-    float* Csm = stQ + 32 * N;          // N x ncol
+    const int Mp = (M + 3) & ~3, Np = (N + 3) & ~3;
+    float* Asm = esm;                   // (L Q)^T, Np x Mp
+    float* stL = Asm + Np * Mp;         // 32 x (Mp + 4)
+    float* stQ = stL + 32 * (Mp + 4);   // 32 x (Np + 4)
+    float* Csm = stQ + 32 * (Np + 4);   // Np x (column chunk rounded up to 4)
     __syncthreads();
     rows_times_cols(Lrows, M, Sj.n, Dinv, np, cols, N, Asm, stL, stQ);
     if (rank == 0) {
@@ -1122,8 +1163,9 @@ cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status,
 }
 
 size_t elim_smem_bytes(int nmv, int cw) {
-    // Asm (nmv^2) + stL (nmv*32) + stQ (32*nmv) + Csm (nmv * cw)
-    return sizeof(float) * ((size_t)nmv * nmv + 64 * (size_t)nmv + (size_t)nmv * cw) + 16;
+    // Asm (nmv4^2) + stL, stQ (32 (nmv4 + 4) each) + Csm (nmv4 cw4), with nmv4 / cw4 rounded up to 4
+    const size_t n4 = ((size_t)nmv + 3) & ~size_t(3), c4 = ((size_t)cw + 3) & ~size_t(3);
+    return sizeof(float) * (n4 * n4 + 64 * (n4 + 4) + n4 * c4) + 16;
 }
 
 cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, cudaStream_t s) {

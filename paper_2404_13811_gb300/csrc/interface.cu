@@ -16,7 +16,10 @@
 namespace cg = cooperative_groups;
 
 constexpr int GJ_NB = 32;   // panel width
-constexpr int GJ_CL = 4;    // CTAs per cluster (one cluster per slab)
+constexpr int GJ_CL = 4;    // CTAs per cluster of the Schur update (one cluster per eliminated slab)
+// CTAs per cluster of the slab LU inverse (one cluster per slab): 8 when a
+// launch's slabs all fit on the GPU as 8-CTA clusters at once, else 4
+constexpr int LU_CL_MIN = 4, LU_CL_MAX = 8;
 constexpr int GJ_THREADS = 512;
 constexpr int GJ_NB_WARPS = GJ_THREADS / 32;
 constexpr int PUB_PAR = GJ_NB_WARPS * GJ_NB;   // one parity of the slab LU's published panel rows
@@ -844,12 +847,13 @@ template <int RPT>
 __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int e = blockIdx.x / GJ_CL;
+    const int CL = (int)cluster.num_blocks();
+    const int e = blockIdx.x / CL;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
     const int np = I.npad;
     const int npan = (np + GJ_NB - 1) / GJ_NB;
-    const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
+    const int ncmax = ((npan + CL - 1) / CL) * GJ_NB;
     extern __shared__ __align__(16) float lsm[];
     float* Ps = lsm;                           // [c][r], GJ_NB * np
     float* Xs = Ps + GJ_NB * np;                          // phase 1 [c][jj] (ld ncmax), phase 2 [jj][r]
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     }
     if (tid == 0) {
         int c = 0;
-        for (int q = rank; q < npan; q += GJ_CL)
+        for (int q = rank; q < npan; q += CL)
             for (int j = q * GJ_NB; j < min(np, (q + 1) * GJ_NB); ++j) ownc[c++] = j;
         nown = c;
     }
@@ -1027,7 +1031,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             if (lane + 32 < naff) col[aff[lane + 32]] = v1;
         }
         __syncthreads();
-        if (q % GJ_CL == rank)
+        if (q % CL == rank)
             for (int c = warp; c < b; c += nwarp)
                 for (int r = k0 + lane; r < np; r += 32) A[(size_t)(k0 + c) * np + r] = Ps[c * np + r];
         // U12 = L11^-1 A12 on owned trailing columns (zero on the others): the
@@ -1135,7 +1139,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
 
 size_t lu_smem(int np, int xch) {
     const int npan = (np + GJ_NB - 1) / GJ_NB;
-    const int ncmax = ((npan + GJ_CL - 1) / GJ_CL) * GJ_NB;
+    const int ncmax = ((npan + LU_CL_MIN - 1) / LU_CL_MIN) * GJ_NB;   // the larger of the two cluster sizes' needs
     const size_t up = std::max((size_t)GJ_NB * ncmax, (size_t)np);
     const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)xch * np);
     if (np > 2 * GJ_THREADS) return (size_t)-1;   // two panel rows per thread at most
@@ -1157,9 +1161,34 @@ cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status,
         if (e != cudaSuccess) return e;
         set_smem[two] = smem;
     }
+    // 8-CTA clusters when the launch's slabs all fit at once (the query runs
+    // on the first, eager launch of a configuration and is kept)
+    static int max8[2] = {-1, -1};
+    static size_t max8_smem[2] = {0, 0};
+    if (max8[two] < 0 || max8_smem[two] != smem) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(LU_CL_MAX);
+        cfg.blockDim = dim3(GJ_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = LU_CL_MAX;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            n = 0;
+        }
+        max8[two] = n;
+        max8_smem[two] = smem;
+    }
+    const int cl = nel <= max8[two] ? LU_CL_MAX : LU_CL_MIN;
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel, &status};
-    return launch_cluster(kern, nel * GJ_CL, GJ_THREADS, smem, s, args);
+    return launch_cluster(kern, nel * cl, GJ_THREADS, smem, s, args, cl);
 }
 
 size_t elim_smem_bytes(int nmv, int cw) {

@@ -215,10 +215,20 @@ __device__ void factor_box(const Box& B, const Ops& O, T* Sinv, T* cys, T* cxs, 
 }
 
 // One warp sweeps in place: on entry w holds the scaled right-hand side, on
-// exit the scaled solution.
+// exit the scaled solution.  The FP32 form reads rows of the symmetric line
+// blocks as float4 (warp_sweeps_f32, after the CTA-wide helpers below).
+__device__ void warp_sweeps_f32(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* z,
+                                int b, int nb);
+
 template <typename T>
 __device__ void warp_sweeps(const T* __restrict__ Sinv, const T* __restrict__ cys, T* w, T* zbuf,
                             int b, int nb) {
+    if constexpr (std::is_same<T, float>::value) {
+        if ((b & 3) == 0) {
+            warp_sweeps_f32(Sinv, cys, w, zbuf, b, nb);
+            return;
+        }
+    }
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < nb; ++j) {
         if (lane < b) {
@@ -426,6 +436,35 @@ __device__ void warp0_sweeps(const float* __restrict__ Sinv, const float* __rest
         }
     }
     __syncthreads();
+}
+
+// The FP32 sweeps of one warp (as warp0_sweeps, b a multiple of 4) for a
+// warp that owns its right-hand side; no block barrier.
+__device__ void warp_sweeps_f32(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* z,
+                                int b, int nb) {
+    const int lane = threadIdx.x & 31;
+    const size_t bb = (size_t)b * b;
+    float4 s4[8];
+    float cur = 0.f;
+    for (int j = 0; j < nb; ++j) {
+        load_srow(s4, Sinv + j * bb, b, lane);
+        float zj = 0.f;
+        if (lane < b) zj = w[j * b + lane] + (j > 0 ? cys[(j - 1) * b + lane] * cur : 0.f);
+        z[lane] = zj;
+        __syncwarp();
+        cur = sline_row_dot(Sinv + j * bb, z, b, lane, s4);
+        if (lane < b) w[j * b + lane] = cur;
+        __syncwarp();
+    }
+    for (int j = nb - 2; j >= 0; --j) {
+        load_srow(s4, Sinv + j * bb, b, lane);
+        z[lane] = lane < b ? cys[j * b + lane] * cur : 0.f;
+        const float wf = lane < b ? w[j * b + lane] : 0.f;
+        __syncwarp();
+        cur = wf + sline_row_dot(Sinv + j * bb, z, b, lane, s4);
+        if (lane < b) w[j * b + lane] = cur;
+        __syncwarp();
+    }
 }
 
 template <typename T>

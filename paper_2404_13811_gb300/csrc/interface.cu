@@ -909,6 +909,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         {
             float x[RPT][GJ_NB];
             int lp[RPT];
+            const bool wact = k0 + warp * 32 < np;   // the warp holds at least one panel row
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {
                 const int r = k0 + tid + i * nt;
@@ -920,6 +921,12 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             for (int c = 0; c < b; ++c) {
                 const int r0 = k0 + c, par = c & 1;
                 float* pb = pub + par * PUB_PAR;            // [warp][GJ_NB] candidate rows
+                if (!wact) {
+                    // a warp without panel rows only takes part in the column's barrier
+                    if (lane == 0) pkey[par * GJ_NB_WARPS + warp] = 0u;
+                    __syncthreads();
+                    continue;
+                }
                 unsigned key = 0u;   // 0: no candidate; a candidate's key is at least 1024 (np <= 1024)
                 int ks = -1;
 #pragma unroll

@@ -864,6 +864,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     int* qpos = ownc + ncmax;                  // np
     float* pub = reinterpret_cast<float*>(qpos + np);   // 2 x PUB_PAR candidate rows published per column
     unsigned* pkey = reinterpret_cast<unsigned*>(pub + PUB_FLOATS);   // 2 x GJ_NB_WARPS pivot keys
+    int* rowperm = reinterpret_cast<int*>(pkey + 2 * GJ_NB_WARPS);    // np: original row at each position
     __shared__ int nown;
     __shared__ int aff[2 * GJ_NB];
     __shared__ int naff;
@@ -881,6 +882,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
             for (int j = q * GJ_NB; j < min(np, (q + 1) * GJ_NB); ++j) ownc[c++] = j;
         nown = c;
     }
+    for (int i = tid; i < np; i += nt) rowperm[i] = i;
     bool singular = false;
     // ---------------- phase 1: P A = L U ----------------
     for (int q = 0; q < npan; ++q) {
@@ -1025,6 +1027,13 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
         for (int i = k0 + tid; i < np; i += nt)
             if (qpos[i] != i) aff[atomicAdd(&naff, 1)] = i;
         __syncthreads();
+        {
+            // the panel's interchanges applied to the row permutation
+            const int na = naff;
+            const int rv = tid < na ? rowperm[qpos[aff[tid]]] : 0;
+            __syncthreads();
+            if (tid < na) rowperm[aff[tid]] = rv;
+        }
         const int no = nown;
         for (int jj = warp; jj < no; jj += nwarp) {
             const int j = ownc[jj];
@@ -1096,16 +1105,7 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     cluster.sync();
     if (!active) return;
     // ---------------- phase 2: owned columns of the inverse ----------------
-    if (tid == 0) {
-        int* rowperm = (int*)Upy;  // rowperm[i] = original row at position i
-        for (int i = 0; i < np; ++i) rowperm[i] = i;
-        for (int c = 0; c < np; ++c) {
-            const int p = piv[c], t0 = rowperm[c];
-            rowperm[c] = rowperm[p];
-            rowperm[p] = t0;
-        }
-        for (int i = 0; i < np; ++i) qpos[rowperm[i]] = i;
-    }
+    for (int i = tid; i < np; i += nt) qpos[rowperm[i]] = i;   // the inverse permutation
     __syncthreads();
     const int no = nown;
     for (int j0 = 0; j0 < no; j0 += XCH) {
@@ -1151,7 +1151,7 @@ size_t lu_smem(int np, int xch) {
     const size_t xs = std::max((size_t)GJ_NB * ncmax, (size_t)xch * np);
     if (np > 2 * GJ_THREADS) return (size_t)-1;   // two panel rows per thread at most
     return sizeof(float) * ((size_t)GJ_NB * np + xs + up + PUB_FLOATS) +
-           sizeof(int) * ((size_t)np + ncmax + np + 2 * GJ_NB_WARPS) + 16;
+           sizeof(int) * ((size_t)np + ncmax + np + 2 * GJ_NB_WARPS + np) + 16;
 }
 
 

@@ -572,31 +572,40 @@ __global__ void k_if_residualT(IfPtrs I, const SubDev* sub, const int* col_item,
 // B_l^T for the eliminations of one level: v_jm -= Cdn_j^T (Dinv_j[:, vrows]^T v_j)
 // (up = 0) or v_jp -= Cup_j^T (Dinv_j[:, mrows]^T v_j) (up = 1).  Each
 // surviving slab receives from one elimination per launch.
-__global__ void __launch_bounds__(256) k_bcr_bwdT(IfPtrs I, const ElimDev* el, int nel, int up) {
-    extern __shared__ float tsm[];
-    const int e = blockIdx.x;
-    if (e >= nel) return;
+__global__ void __launch_bounds__(SW_T) k_bcr_bwdT(IfPtrs I, const ElimDev* el, int nel, int up) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / SW_CL;   // the grid is nel clusters
+    extern __shared__ __align__(16) float tsm[];
     const ElimDev E = el[e];
-    if (up && E.jp < 0) return;
+    if (up && E.jp < 0) return;   // uniform over the cluster
     const SlabDev Sj = I.slabs[E.j];
     const int np = I.npad;
     const float* Dinv = I.Dinv + Sj.offD;
     const int* rows = I.idx + Sj.offIdx + (up ? 0 : Sj.nm);
     const int nq = up ? Sj.nm : Sj.nv;
-    float* vj = tsm;
-    float* t = tsm + np;
-    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) vj[r] = I.bq[Sj.col0 + r];
+    float* vj = tsm;           // n_j
+    float* tl = tsm + np;      // this CTA's entries of t, at their own positions
+    float* t = tsm + 2 * np;   // nq
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, nwarp = nt >> 5;
+    for (int r = tid; r < Sj.n; r += nt) vj[r] = I.bq[Sj.col0 + r];
     __syncthreads();
-    for (int q = warp; q < nq; q += nwarp) {
+    // t = Dinv_j[:, rows]^T v_j, the entries split over the cluster in contiguous chunks
+    const int kw = (nq + SW_CL - 1) / SW_CL, k0 = min(nq, rank * kw), k1 = min(nq, k0 + kw);
+    for (int q = k0 + warp; q < k1; q += nwarp) {
         const float acc = warp_dot(Dinv + (size_t)rows[q] * np, vj, Sj.n);
-        if ((threadIdx.x & 31) == 0) t[q] = acc;
+        if ((tid & 31) == 0) tl[q] = acc;
     }
-    __syncthreads();
+    cluster.sync();
+    for (int q = tid; q < nq; q += nt) t[q] = cluster.map_shared_rank(tl, q / kw)[q];
+    cluster.sync();   // no CTA leaves while its entries may still be read
+    // b_t -= C^T t over this CTA's chunk of the target entries
     const SlabDev St = I.slabs[up ? E.jp : E.jm];
     const float* Cq = I.Cup + (up ? Sj.offCup : Sj.offCdn);
     float* bt = I.bq + St.col0;
-    for (int c = threadIdx.x; c < St.n; c += blockDim.x) {
+    const int cwd = (St.n + SW_CL - 1) / SW_CL, c0 = min(St.n, rank * cwd), c1 = min(St.n, c0 + cwd);
+    for (int c = c0 + tid; c < c1; c += nt) {
         float acc = 0.f;
         for (int q = 0; q < nq; ++q) acc += Cq[(size_t)q * Sj.ldc + c] * t[q];
         bt[c] -= acc;
@@ -605,48 +614,58 @@ __global__ void __launch_bounds__(256) k_bcr_bwdT(IfPtrs I, const ElimDev* el, i
 
 // F_l^T for the eliminations of one level:
 // b_j -= Rup^T b_jm[mrows_jm] + Rdn^T b_jp[vrows_jp], then b_j <- Dinv_j^T b_j.
-__global__ void __launch_bounds__(256) k_bcr_fwdT(IfPtrs I, const ElimDev* el, int nel) {
-    extern __shared__ float fts[];
-    const int e = blockIdx.x;
-    if (e >= nel) return;
+__global__ void __launch_bounds__(SW_T) k_bcr_fwdT(IfPtrs I, const ElimDev* el, int nel) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int e = blockIdx.x / SW_CL;
+    extern __shared__ __align__(16) float fts[];
     const ElimDev E = el[e];
     const SlabDev Sj = I.slabs[E.j];
-    const int np = I.npad;
-    float* bs = fts;          // n_j
-    float* gv = fts + np;     // neighbour rows
-    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) bs[r] = I.bq[Sj.col0 + r];
-    if (E.jm >= 0 && E.jm != E.j) {
-        const SlabDev Sm = I.slabs[E.jm];
+    const int np = I.npad, n = Sj.n;
+    float* part = fts;         // np: neighbour terms over this CTA's chunk of coupling rows
+    float* bs = fts + np;      // np: b_j after the neighbour terms
+    float* gv = fts + 2 * np;  // 2 np: the neighbours' coupled entries (m rows, then v rows)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, nwarp = nt >> 5;
+    const bool hm = E.jm >= 0 && E.jm != E.j, hp = E.jp >= 0;
+    SlabDev Sm{}, Sp{};
+    int nmm = 0, nvp = 0;
+    if (hm) {
+        Sm = I.slabs[E.jm];
+        nmm = Sm.nm;
         const int* mrows_m = I.idx + Sm.offIdx;
-        const float* Rup = I.Rup + Sj.offRup;   // nm_jm x n_j
-        __syncthreads();
-        for (int q = threadIdx.x; q < Sm.nm; q += blockDim.x) gv[q] = I.bq[Sm.col0 + mrows_m[q]];
-        __syncthreads();
-        for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
-            float acc = 0.f;
-            for (int q = 0; q < Sm.nm; ++q) acc += Rup[(size_t)q * Sj.n + r] * gv[q];
-            bs[r] -= acc;
-        }
+        for (int q = tid; q < nmm; q += nt) gv[q] = I.bq[Sm.col0 + mrows_m[q]];
     }
-    if (E.jp >= 0) {
-        const SlabDev Sp = I.slabs[E.jp];
+    if (hp) {
+        Sp = I.slabs[E.jp];
+        nvp = Sp.nv;
         const int* vrows_p = I.idx + Sp.offIdx + Sp.nm;
-        const float* Rdn = I.Rdn + Sj.offRdn;   // nv_jp x n_j
-        __syncthreads();
-        for (int q = threadIdx.x; q < Sp.nv; q += blockDim.x) gv[q] = I.bq[Sp.col0 + vrows_p[q]];
-        __syncthreads();
-        for (int r = threadIdx.x; r < Sj.n; r += blockDim.x) {
-            float acc = 0.f;
-            for (int q = 0; q < Sp.nv; ++q) acc += Rdn[(size_t)q * Sj.n + r] * gv[q];
-            bs[r] -= acc;
-        }
+        for (int q = tid; q < nvp; q += nt) gv[nmm + q] = I.bq[Sp.col0 + vrows_p[q]];
     }
     __syncthreads();
+    const float* Rup = I.Rup + Sj.offRup;   // nm_jm x n_j
+    const float* Rdn = I.Rdn + Sj.offRdn;   // nv_jp x n_j
+    const int nq = nmm + nvp;
+    const int kw = (nq + SW_CL - 1) / SW_CL, k0 = min(nq, rank * kw), k1 = min(nq, k0 + kw);
+    for (int r = tid; r < n; r += nt) {
+        float acc = 0.f;
+        for (int q = k0; q < k1; ++q)
+            acc += (q < nmm ? Rup[(size_t)q * n + r] : Rdn[(size_t)(q - nmm) * n + r]) * gv[q];
+        part[r] = acc;
+    }
+    cluster.sync();   // partials complete; every read of b_j below precedes the writes after the next barrier
+    for (int r = tid; r < n; r += nt) {
+        float acc = 0.f;
+        for (int q = 0; q < SW_CL; ++q) acc += cluster.map_shared_rank(part, q)[r];
+        bs[r] = I.bq[Sj.col0 + r] - acc;
+    }
+    cluster.sync();   // no CTA leaves while its partials may still be read, b_j read by all
+    // b_j <- Dinv_j^T b_j, the rows split over the cluster
     const float* Dinv = I.Dinv + Sj.offD;
-    for (int r = warp; r < Sj.n; r += nwarp) {
-        const float acc = warp_dot(Dinv + (size_t)r * np, bs, Sj.n);
-        if ((threadIdx.x & 31) == 0) I.bq[Sj.col0 + r] = acc;
+    const int rw = (n + SW_CL - 1) / SW_CL, r0 = min(n, rank * rw), r1 = min(n, r0 + rw);
+    for (int r = r0 + warp; r < r1; r += nwarp) {
+        const float acc = warp_dot(Dinv + (size_t)r * np, bs, n);
+        if ((tid & 31) == 0) I.bq[Sj.col0 + r] = acc;
     }
 }
 
@@ -662,16 +681,35 @@ cudaError_t if_residualT(const IfPtrs& I, const SubDev* sub, const int* col_item
     return cudaGetLastError();
 }
 
+static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
+                                  void** args, int cl = GJ_CL) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
 cudaError_t bcr_bwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, int up, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_bwdT<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel, up);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel, &up};
+    return launch_cluster((const void*)k_bcr_bwdT, nel * SW_CL, SW_T, sizeof(float) * 3 * (size_t)nmax, s, args, SW_CL);
 }
 
 cudaError_t bcr_fwdT(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
-    k_bcr_fwdT<<<nel, 256, sizeof(float) * 2 * nmax, s>>>(I, el, nel);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel};
+    return launch_cluster((const void*)k_bcr_fwdT, nel * SW_CL, SW_T, sizeof(float) * 4 * (size_t)nmax, s, args, SW_CL);
 }
 
 cudaError_t if_updateT(const IfPtrs& I, double* y, int n, cudaStream_t s) {
@@ -700,23 +738,6 @@ cudaError_t bcr_fill(const IfPtrs& I, int nslab, cudaStream_t s) {
 cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int first, cudaStream_t s) {
     k_if_residual<<<(nrows + 255) / 256, 256, 0, s>>>(I, row_member, nrows, first);
     return cudaGetLastError();
-}
-
-static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
-                                  void** args, int cl = GJ_CL) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nblocks);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {

@@ -222,6 +222,12 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
  * fixed only up to a constant).  Needs a solution (MRCM_ERR_STATE). */
 int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs);
 
+/* The same reverse pass with the seeds in (velocity, pressure) order and host
+ * arrays: dL_du [total cells][2 * dim], dL_dp [total cells] (either may be
+ * NULL), dL_dlogK [total cells] output; all caller-owned host memory (the
+ * call synchronises).  Returns and errors as mrcm_adjoint. */
+int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, double* dL_dlogK);
+
 /* Counters of the last calls: ints[0] = number of subdomains (all members),
  * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
  * last solve, ints[3] = largest local refinement count of the last

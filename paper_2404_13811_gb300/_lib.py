@@ -42,7 +42,7 @@ class mrcm_params(C.Structure):
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
            "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_set_permeability",
-           "mrcm_adjoint", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_destroy", "mrcm_last_error"]
+           "mrcm_adjoint", "mrcm_backward", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_destroy", "mrcm_last_error"]
 PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph", "interface_lu"]
 
 _lib = None
@@ -77,6 +77,7 @@ def load(path=LIBPATH):
     lib.mrcm_fluxes_static.argtypes = [vp, C.c_int, vp, vp]
     lib.mrcm_set_permeability.argtypes = [vp, vp, C.c_int, C.c_int]
     lib.mrcm_adjoint.argtypes = [vp, vp, vp, vp, C.c_int]
+    lib.mrcm_backward.argtypes = [vp, vp, vp, vp]
     lib.mrcm_stats.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_double), C.c_int]
     lib.mrcm_profile.argtypes = [vp, C.c_int]
     lib.mrcm_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
@@ -218,6 +219,14 @@ def mrcm_adjoint(h, gp, gu, g_logK):
     pp = _ptr(gp)[0] if gp is not None else None
     up = _ptr(gu)[0] if gu is not None else None
     _check(lib, h, lib.mrcm_adjoint(h, C.c_void_p(pp), C.c_void_p(up), C.c_void_p(op), int(dev)))
+
+
+def mrcm_backward(h, dL_du, dL_dp, dL_dlogK):
+    """Host (numpy) seeds in (velocity, pressure) order; either may be None."""
+    lib = load()
+    up = _ptr(dL_du)[0] if dL_du is not None else None
+    pp = _ptr(dL_dp)[0] if dL_dp is not None else None
+    _check(lib, h, lib.mrcm_backward(h, C.c_void_p(up), C.c_void_p(pp), C.c_void_p(_ptr(dL_dlogK)[0])))
 
 
 def mrcm_stats(h):

@@ -1163,6 +1163,10 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
     return 0;
 }
 
+int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, double* dL_dlogK) {
+    return mrcm_adjoint(h, dL_dp, dL_du, dL_dlogK, 0);
+}
+
 int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");

@@ -183,20 +183,6 @@ __device__ void build_ops3(const Box3& B, const MemberDev& md, const DevPtrs& P,
     __syncthreads();
 }
 
-// (A x)_t of the unscaled FP64 operator
-__device__ __forceinline__ double applyA3(const Box3& B, const Ops3& O, const double* x, int t) {
-    const unsigned char m = O.nb[t];
-    const int s1 = B.n[B.a0], s2 = B.b;
-    double s = O.cd[t] * x[t];
-    if (m & 1) s -= O.c0[t - 1] * x[t - 1];
-    if (m & 2) s -= O.c0[t] * x[t + 1];
-    if (m & 4) s -= O.c1[t - s1] * x[t - s1];
-    if (m & 8) s -= O.c1[t] * x[t + s1];
-    if (m & 16) s -= O.c2[t - s2] * x[t - s2];
-    if (m & 32) s -= O.c2[t] * x[t + s2];
-    return s;
-}
-
 // (A x)_t of the unscaled FP64 operator with the couplings read from the
 // global face coefficients (the mixed form keeps no coupling arrays on chip
 // during the solves)

@@ -243,16 +243,34 @@ __device__ void apply_coupling(const float* AT, int M, int M2, const float* Cg, 
 #pragma unroll
                     for (int y = 0; y < 4; ++y) acc[x][y] += av[x] * cv[y];
             }
+            if (ACCUM_INTO_D) {
+                // the tile's 16 entries of D read before any is written (the target
+                // rows are distinct), so that the reads are in flight together
+                float dv[4][4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const int r = 4 * i + x;
-                if (r >= M) continue;
+                for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) {
-                    const int c = 4 * jc + y;
-                    if (c >= cw) continue;
-                    if (ACCUM_INTO_D) D[(size_t)(c0 + c) * np + rows[r]] -= acc[x][y];
-                    else Cout[(size_t)r * ldout + c0 + c] = -acc[x][y];
+                    for (int y = 0; y < 4; ++y) {
+                        const int r = 4 * i + x, c = 4 * jc + y;
+                        dv[x][y] = (r < M && c < cw) ? D[(size_t)(c0 + c) * np + rows[r]] : 0.f;
+                    }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const int r = 4 * i + x, c = 4 * jc + y;
+                        if (r < M && c < cw) D[(size_t)(c0 + c) * np + rows[r]] = dv[x][y] - acc[x][y];
+                    }
+            } else {
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int r = 4 * i + x;
+                    if (r >= M) continue;
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const int c = 4 * jc + y;
+                        if (c < cw) Cout[(size_t)r * ldout + c0 + c] = -acc[x][y];
+                    }
                 }
             }
         }

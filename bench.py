@@ -262,10 +262,7 @@ def run_gpu(args, rank, world):
     clocks = clk.stop()
     ms_fp64, _ = timed(solvers["fp64"], max(2, args.steps // 4), 1)
     torch.cuda.synchronize()
-    if world > 1:
-        t = torch.tensor([ms_mixed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_mixed = float(t.item())
+    ms_mixed = max_over_ranks(ms_mixed, world, "cuda")
     ms_step = ms_mixed / args.steps
     value = ncell * world / (ms_step * 1e-3)
     fp64_value = ncell / (ms_fp64 / max(2, args.steps // 4) * 1e-3)
@@ -430,6 +427,18 @@ def run_other(args):
                                "value": prob.ncells / ((ms_f + ms_g) * 1e-3)}
             s.close()
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values: a replicated job takes as long as its
+    slowest rank.  device: "cuda" under NCCL, "cpu" under gloo."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------

@@ -160,7 +160,8 @@ int mrcm_smooth(mrcm_handle* h, int n_steps);
  * into a CUDA graph on the handle's stream and from then on replays it with
  * one graph launch; after each replay the interface residual and the local
  * status are read back (the call synchronises) and MRCM_ERR_NO_CONVERGENCE
- * is returned if the captured refinement count no longer reaches ir_tol.
+ * is returned if the replayed refinement (the eager solve's number of steps)
+ * leaves an interface residual above 1e3 ir_tol.
  * The graph is recaptured when n_steps changes.  Inputs are the ones given
  * at creation (the batching form of the method: uneven subdomains and whole
  * ensembles in one submission). */

@@ -1039,7 +1039,10 @@ int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
         }
         const bool prof = h->prof;
         h->prof = false;  // no profiling events inside the graph
-        h->graph_nit = h->if_iters + 1;
+        // the eager solve's refinement count: the same inputs and no order-
+        // dependent sums make the captured sequence reproduce its result (the
+        // residual is still checked after every launch)
+        h->graph_nit = h->if_iters;
         // capture on a private stream (the legacy default stream cannot be captured)
         if (!h->cap_stream) CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
         CUDA_TRY(h, cudaStreamSynchronize(st));

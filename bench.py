@@ -222,6 +222,27 @@ def run_gpu(args, rank, world):
             p, u = s.fluxes()
             ep, eu = O.rel_errors(prob, p, u, ref.p, ref.u)
             errs[name] = {"flux_rel_l2": eu, "pressure_rel_l2": ep}
+    # the equal-error comparison: the mixed form with the refinement tolerance
+    # tightened towards the FP64 form's flux error (the first tolerance whose
+    # local and interface refinements converge)
+    from paper_2404_13811_gb300 import _lib as L
+    eq = {"note": "mixed form with ir_tol tightened towards the FP64 form's flux error"}
+    for tol in (1e-14, 1e-13):
+        s_eq = None
+        try:
+            s_eq = make("mixed", tol=tol)
+            step(s_eq)
+            eq["ir_tol"] = tol
+            if rank == 0 and not args.no_oracle:
+                p, u = s_eq.fluxes()
+                ep, eu = O.rel_errors(prob, p, u, ref.p, ref.u)
+                eq["flux_rel_l2"], eq["pressure_rel_l2"] = eu, ep
+            solvers["mixed_eq"] = s_eq
+            break
+        except L.MrcmError as exc:
+            eq["unconverged_at_" + f"{tol:.0e}"] = str(exc)
+            if s_eq is not None:
+                s_eq.close()
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
 
@@ -261,6 +282,11 @@ def run_gpu(args, rank, world):
     ms_mixed, tm = timed(solvers["mixed"], args.steps, args.warmup, profile=True)
     clocks = clk.stop()
     ms_fp64, _ = timed(solvers["fp64"], max(2, args.steps // 4), 1)
+    if "mixed_eq" in solvers:
+        ms_eq, _ = timed(solvers["mixed_eq"], max(2, args.steps // 4), 1)
+        eq["ms_per_step"] = ms_eq / max(2, args.steps // 4)
+        eq["value"] = ncell / (eq["ms_per_step"] * 1e-3)
+        eq["unit"] = "cells/s"
     torch.cuda.synchronize()
     ms_mixed = max_over_ranks(ms_mixed, world, "cuda")
     ms_step = ms_mixed / args.steps
@@ -328,6 +354,7 @@ def run_gpu(args, rank, world):
                    "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas{world}",
                    "step": "mrcm_run: the whole step replayed as one captured CUDA graph"},
         "fp64_form": {"value": fp64_value, "unit": "cells/s", "ms_per_step": 1e3 * ncell / fp64_value},
+        "mixed_equal_error": eq,
         "errors_vs_oracle": errs, "phase_ms_per_step": phase_ms, "launches_per_step": launches,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
         "subdomain_solves_per_s": local_solves_per_step(case) * world / (ms_step * 1e-3),

@@ -140,10 +140,47 @@ def test_call_order_enforced():
     assert np.array_equal(p1, p2) and np.array_equal(u1, u2)
 
 
+_CHANNEL512 = {}
+
+
+def _channel512():
+    """The 512x512 workload and its oracle result, computed once per session."""
+    if not _CHANNEL512:
+        case = I.config_channel2d()
+        pm = case.params
+        ref = O.mrcm_os(case.problem, case.partition.sub, case.partition.overlap, pm.space,
+                        pm.alpha_basis, pm.alpha_smooth, pm.n_smooth, keep_stages=True)
+        _CHANNEL512["v"] = (case, ref)
+    return _CHANNEL512["v"]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_size_channel_512(precision):
     """The 512x512 channelised workload (32x32 subdomains, P1, overlap 4,
-    8 smoothing steps) in the launch configuration the benchmark times,
-    compared with the oracle on every cell."""
-    case = I.config_channel2d()
-    _run_compare(case, precision, stages=(8,))
+    8 smoothing steps) through the eager calls, compared with the oracle on
+    every cell."""
+    case, ref = _channel512()
+    s = _solver(case, precision)
+    s.build_basis()
+    s.solve_interface()
+    s.smooth(case.params.n_smooth)
+    p, u = s.fluxes()
+    s.close()
+    rp, ru = ref.stages[f"smooth{case.params.n_smooth}"]
+    _compare(case.problem, p, u, rp, ru, TOL[precision], f"{case.name} {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_channel_512_captured_step(precision):
+    """The same workload as the benchmark times it: mrcm_run with the step
+    captured as one CUDA graph -- the first call (eager run, capture, one
+    replay) and a second call (replay only), each compared with the oracle
+    on every cell."""
+    case, ref = _channel512()
+    rp, ru = ref.stages[f"smooth{case.params.n_smooth}"]
+    s = _solver(case, precision)
+    for call in range(2):
+        s.run(case.params.n_smooth, graph=True)
+        p, u = s.fluxes()
+        _compare(case.problem, p, u, rp, ru, TOL[precision], f"{case.name} {precision} graph call {call}")
+    s.close()

@@ -138,7 +138,10 @@ int mrcm_build_basis(mrcm_handle* h);   /* any stage; restarts the pipeline */
 
 /* Algorithm 1, Step 5: assembles the interface rows of Eqs.
  * (int_ujump)-(int_pjump) tested with all of M_H x V_H, solves them for the
- * coefficients X (FP32 factorisation + FP64 iterative refinement to ir_tol),
+ * coefficients X (FP32 factorisation + FP64 iterative refinement to ir_tol;
+ * when the refinement stops contracting, restarted FP64 GMRES preconditioned
+ * by the same FP32 factorisation continues from its iterate, and mrcm_run
+ * then runs the problem eagerly instead of replaying a captured step),
  * and assembles u = ubar + sum_j X_j Phi_j, p = pbar + sum_j X_j Psi_j
  * (Eqs. (addu), (addp), (uhatphat)).  Pure-Neumann members are solved in the
  * gauge X^0_0 = 0 and reported with zero-mean pressure.  Synchronises the

@@ -41,6 +41,11 @@ cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int f
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s);
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s);
+cudaError_t kry_to_bq(const IfPtrs& I, const double* v, int n, cudaStream_t s);
+cudaError_t kry_from_bq(const IfPtrs& I, double* z, int n, cudaStream_t s);
+cudaError_t kry_axpby(double* y, const double* x, double a, double b, int n, cudaStream_t s);
+cudaError_t kry_dot(const double* a, const double* b, int n, double* part, cudaStream_t s);
+int kry_blocks();
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
 size_t elim_smem_bytes(int nmv, int cw);
 size_t lu_smem(int np, int xch);
@@ -165,6 +170,8 @@ struct mrcm_handle {
     // stats
     int if_iters = 0;
     double if_res = 0.0;
+    bool if_krylov = false;       // the last interface solve needed the GMRES fallback
+    double* d_kry = nullptr;      // its workspace (allocated on first use)
     int loc_ir = 0;
     long long local_solves = 0;
 };
@@ -764,6 +771,22 @@ static int issue_residual(mrcm_handle* h) {
     return 0;
 }
 
+// the FP32 block-cyclic-reduction sweeps on I.bq, in place
+static int issue_bcr_sweeps(mrcm_handle* h) {
+    const int nlev = (int)h->levels.size();
+    for (int l = 0; l < nlev; ++l) {
+        const Level& L = h->levels[l];
+        CUDA_TRY(h, bcr_fwd(h->I, h->d_elims + L.off, L.count, h->npad, h->stream));
+        h->launches[2] += 1;
+    }
+    for (int l = nlev - 2; l >= 0; --l) {
+        const Level& L = h->levels[l];
+        CUDA_TRY(h, bcr_bwd(h->I, h->d_elims + L.off, L.count, h->npad, h->stream));
+        h->launches[2] += 1;
+    }
+    return 0;
+}
+
 static int issue_if_sweeps(mrcm_handle* h) {
     Phase ph(h, 2);
     const int nlev = (int)h->levels.size();
@@ -965,6 +988,118 @@ int mrcm_build_basis(mrcm_handle* h) {
     return 0;
 }
 
+// Interface fallback when the refinement stalls: restarted GMRES in FP64 on
+// G X = rhs, right-preconditioned by the FP32 reduction (the row scaling, the
+// sweeps and the column scaling of one refinement step), started from the
+// refined iterate.  G v is the residual kernel with x = v and a zero
+// right-hand side (it returns -G v).  Dot products: per-block partial sums
+// added on the host in a fixed order.  Ends when the library's residual test
+// (worst member, max norm relative to the right-hand side) reaches ir_tol.
+static int krylov_interface(mrcm_handle* h, double* worst_out) {
+    const int n = h->nif, m = 30, max_restarts = 20;
+    cudaStream_t st = h->stream;
+    const int nb = kry_blocks();
+    if (!h->d_kry) {
+        if (int e = dalloc(h, &h->d_kry, (size_t)(m + 4) * n + (size_t)nb)) return e;
+    }
+    double* V = h->d_kry;                    // (m + 1) x n Krylov basis
+    double* w = V + (size_t)(m + 1) * n;     // n
+    double* u = w + n;                       // n
+    double* zero = u + n;                    // n (zero right-hand side)
+    double* part = zero + n;                 // nb partial sums
+    CUDA_TRY(h, cudaMemsetAsync(zero, 0, sizeof(double) * n, st));
+    std::vector<double> hp(nb);
+    double rhs2 = 0.0;
+    auto dot = [&](const double* a, const double* b, double* out) -> int {
+        CUDA_TRY(h, kry_dot(a, b, n, part, st));
+        CUDA_TRY(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        double acc = 0.0;
+        for (int i = 0; i < nb; ++i) acc += hp[i];
+        *out = acc;
+        return 0;
+    };
+    // z = M^-1 v (through I.bq)
+    auto precond = [&](const double* v, double* z) -> int {
+        CUDA_TRY(h, kry_to_bq(h->I, v, n, st));
+        if (int e = issue_bcr_sweeps(h)) return e;
+        CUDA_TRY(h, kry_from_bq(h->I, z, n, st));
+        return 0;
+    };
+    if (int e = dot(h->I.rhs, h->I.rhs, &rhs2)) return e;
+    // the inner test, on the 2-norm, with a margin for the max-norm test that ends a cycle
+    const double target = 1e-2 * h->mth.ir_tol * std::sqrt(rhs2);
+    IfPtrs J = h->I;   // G v: x = v, rhs = 0, result (-G v) into w
+    J.rhs = zero;
+    J.r = w;
+    double worst = 0.0;
+    for (int rs = 0; rs < max_restarts; ++rs) {
+        // r0 = rhs - G x into I.r; beta = |r0|
+        if (int e = issue_residual(h)) return e;
+        if (int e = read_if_residual(h, &worst)) return e;
+        if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface Krylov iteration diverged");
+        if (worst <= h->mth.ir_tol) break;
+        double beta2 = 0.0;
+        if (int e = dot(h->I.r, h->I.r, &beta2)) return e;
+        const double beta = std::sqrt(beta2);
+        if (beta == 0.0) break;
+        CUDA_TRY(h, kry_axpby(V, h->I.r, 1.0 / beta, 0.0, n, st));
+        std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+        g[0] = beta;
+        int kk = 0;
+        for (int j = 0; j < m; ++j) {
+            kk = j + 1;
+            if (int e = precond(V + (size_t)j * n, u)) return e;
+            J.x = u;
+            CUDA_TRY(h, if_residual(J, h->d_row_member, n, 0, st));   // w = -G u
+            CUDA_TRY(h, kry_axpby(w, w, 0.0, -1.0, n, st));            // w = G u
+            for (int i = 0; i <= j; ++i) {
+                double hij = 0.0;
+                if (int e = dot(w, V + (size_t)i * n, &hij)) return e;
+                H[(size_t)i * m + j] = hij;
+                CUDA_TRY(h, kry_axpby(w, V + (size_t)i * n, -hij, 1.0, n, st));
+            }
+            double hn2 = 0.0;
+            if (int e = dot(w, w, &hn2)) return e;
+            const double hn = std::sqrt(hn2);
+            H[(size_t)(j + 1) * m + j] = hn;
+            // previous rotations on column j, then a new one
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[(size_t)j * m + j], b = hn;
+            const double rr = std::sqrt(a * a + b * b);
+            cs[j] = rr > 0 ? a / rr : 1.0;
+            sn[j] = rr > 0 ? b / rr : 0.0;
+            H[(size_t)j * m + j] = rr;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (hn == 0.0 || std::fabs(g[j + 1]) <= target) break;
+            CUDA_TRY(h, kry_axpby(V + (size_t)(j + 1) * n, w, 1.0 / hn, 0.0, n, st));
+        }
+        // y = H^-1 g (upper triangular kk x kk); x += M^-1 (V y)
+        std::vector<double> y(kk, 0.0);
+        for (int i = kk - 1; i >= 0; --i) {
+            double t = g[i];
+            for (int k = i + 1; k < kk; ++k) t -= H[(size_t)i * m + k] * y[k];
+            const double d = H[(size_t)i * m + i];
+            y[i] = d != 0.0 ? t / d : 0.0;
+        }
+        CUDA_TRY(h, cudaMemsetAsync(w, 0, sizeof(double) * n, st));
+        for (int i = 0; i < kk; ++i) CUDA_TRY(h, kry_axpby(w, V + (size_t)i * n, y[i], 1.0, n, st));
+        if (int e = precond(w, u)) return e;
+        CUDA_TRY(h, kry_axpby(h->I.x, u, 1.0, 1.0, n, st));
+    }
+    // the residual of the final iterate (also leaves I.r and the norms current)
+    if (int e = issue_residual(h)) return e;
+    if (int e = read_if_residual(h, &worst)) return e;
+    *worst_out = worst;
+    return 0;
+}
+
 int mrcm_solve_interface(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_BASIS) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must follow mrcm_build_basis");
@@ -979,6 +1114,8 @@ int mrcm_solve_interface(mrcm_handle* h) {
     std::string hist;
     const int max_it = std::max(8, h->prm.max_ir);
     CUDA_TRY(h, cudaMemsetAsync(h->I.x, 0, sizeof(double) * h->nif, st));
+    double prev = 0.0;
+    bool stalled = false;
     for (;; ++it) {
         rc = issue_residual(h);
         if (rc) return rc;
@@ -990,11 +1127,25 @@ int mrcm_solve_interface(mrcm_handle* h) {
             hist += buf;
             if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
             if (worst <= h->mth.ir_tol || it >= max_it) break;
+            // no longer contracting: the FP32 factor is too poor a preconditioner
+            // for stationary refinement of this system; GMRES takes over
+            if (it >= 2 && worst > 0.9 * prev) {
+                stalled = true;
+                break;
+            }
+            prev = worst;
         }
         rc = issue_if_sweeps(h);
         if (rc) return rc;
     }
     (void)nmem;
+    h->if_krylov = false;
+    if (worst > h->mth.ir_tol && (stalled || it >= max_it)) {
+        rc = krylov_interface(h, &worst);
+        if (rc) return rc;
+        h->if_krylov = true;
+        hist += " (GMRES)";
+    }
     h->if_iters = it;
     h->if_res = worst;
     if (worst > h->mth.ir_tol * 1e3)
@@ -1022,14 +1173,15 @@ int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
     if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
     h->err.clear();
     int rc;
-    if (!use_graph || h->if_iters == 0) {
-        // eager: also fixes the refinement count a captured step will use
+    if (!use_graph || h->if_iters == 0 || h->if_krylov) {
+        // eager: also fixes the refinement count a captured step will use; a
+        // problem whose interface needed the GMRES fallback always runs eagerly
         rc = mrcm_build_basis(h);
         if (rc) return rc;
         rc = mrcm_solve_interface(h);
         if (rc) return rc;
         rc = mrcm_smooth(h, n_steps);
-        if (rc || !use_graph) return rc;
+        if (rc || !use_graph || h->if_krylov) return rc;
     }
     cudaStream_t st = h->stream;
     if (!h->graph_exec || h->graph_steps != n_steps) {

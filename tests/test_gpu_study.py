@@ -12,10 +12,11 @@ Asserted on the configurations whose interface solve converges:
   with l = 2 and with l = 4 is below the one with l = 0;
 * with oversampling (l = 4) MRCM-O needs a large alpha_basis (Sec. 4.2):
   its error at alpha_basis = 1e2 is below the one at 1e-2.
-The interface system's FP32 reduction factor is a preconditioner of FP64
-refinement; at extreme alpha_basis the system is too ill-conditioned for it
-and the refinement stalls (MRCM_ERR_NO_CONVERGENCE): such cells of the table
-read "stall".  The table of relative L2 flux errors is printed (pytest -s).
+At extreme alpha_basis the interface system is too ill-conditioned for
+stationary refinement with its FP32 reduction factor; the solve then
+switches to FP64 GMRES preconditioned by that factor, and every
+configuration of the sweep converges.  The table of relative L2 flux errors
+is printed (pytest -s).
 """
 import numpy as np
 import pytest
@@ -62,7 +63,7 @@ def test_alpha_overlap_smoothing_directions():
     for (alpha, l), errs in table.items():
         row = "stall" if errs is None else "  ".join(f"{e:.2e}" for e in errs)
         print(f"  alpha {alpha:7.0e}  l {l}: " + row)
-    assert all(table[(1.0, l)] is not None for l in OVERLAPS)
+    assert all(v is not None for v in table.values())
     for (alpha, l), e in table.items():
         if e is None:
             continue

@@ -188,10 +188,12 @@ int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells
  * nothing: its multi-block gauge reduction uses a file-scope static device
  * array of 1024 partial sums (8 KB, held by every device that loads the
  * library until the process exits), one per block of 4096 cells, so a member
- * may have at most 4194304 cells (MRCM_ERR_UNSUPPORTED otherwise).  The first
- * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (other streams, other
+ * may have at most 4194304 cells (MRCM_ERR_UNSUPPORTED otherwise).  The
+ * device on which the handle was created must be the current device
+ * (MRCM_ERR_BAD_INPUT otherwise).  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture, and not from two host threads at once.  Every
+ * call shares the array: calls that overlap on the GPU (other streams, other
  * handles) race on it.  Runs on the handle's stream and does not synchronise. */
 int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells);
 

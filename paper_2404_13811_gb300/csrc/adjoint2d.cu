@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_adj_smooth2d(DevPtrs P, Metho
     const int per = 2 * (B.nx + B.ny);
     size_t o = 0;
     auto take = [&](size_t bytes) { unsigned char* p = smem + o; o += align16(bytes); return p; };
-    T* Sinv = (T*)take(sizeof(T) * n * B.nx);
+    T* Sinv = (T*)take(sizeof(T) * sinv_len(B.nx, B.ny, sizeof(T)));
     Ops O;
     O.cd = (double*)take(sizeof(double) * n);
     O.cx = (double*)take(sizeof(double) * n);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_adj_smooth2d(DevPtrs P, Metho
     double* lam = (double*)take(sizeof(double) * per);
     double* rt = (double*)take(sizeof(double) * n);
     T* cys = (T*)take(sizeof(T) * n);
-    T* zbuf = (T*)take(sizeof(T) * 32);
+    T* zbuf = (T*)take(sizeof(T) * 64);   // two line inputs of the twisted sweeps
     double* x = (double*)take(sizeof(double) * n);
     double* mu = (double*)take(sizeof(double) * n);
     T* w = mixed ? (T*)take(sizeof(T) * n) : nullptr;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(AS_WARPS * 32) k_adj_smooth2d(DevPtrs P, Metho
     int* flags = (int*)take(64);
 
     const T* Sg = (const T*)P.fac + (size_t)item * P.fac_stride;
-    for (size_t t = threadIdx.x; t < n * B.nx; t += blockDim.x) Sinv[t] = Sg[t];
+    for (size_t t = threadIdx.x; t < sinv_len(B.nx, B.ny, sizeof(T)); t += blockDim.x) Sinv[t] = Sg[t];
     if (threadIdx.x == 0) flags[0] = 0;
     build_ops(B, md, P, O);
     const double* dd = P.dsc + (size_t)item * P.dsc_stride;
@@ -364,8 +364,8 @@ __host__ __device__ inline size_t adj_carve_bytes(int nx, int ny, int nw, bool p
     const size_t per = 2 * (size_t)(nx + ny);
     size_t s = align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);   // cd cx cy dsc hk
     s += align16(sizeof(double) * per) * 3;                                           // bT bB gbT
-    s += align16(sizeof(T) * n * nx) + align16(sizeof(T) * n) * 2 + align16(sizeof(T) * nx * nx);
-    s += align16(sizeof(T) * 32) + align16(sizeof(T) * 32 * nw);
+    s += align16(sizeof(T) * sinv_len(nx, ny, sizeof(T))) + align16(sizeof(T) * n) * 2;
+    s += align16(sizeof(T) * 64 * nw);
     s += part ? align16(sizeof(double) * n) : 0;
     s += align16(sizeof(double) * n) * 2;                                             // gcx gcy
     s += (align16(sizeof(double) * n) * 3 + (std::is_same<T, float>::value ? align16(sizeof(T) * n) : 0)) * nw;
@@ -400,11 +400,10 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
     O.bT = (double*)take(sizeof(double) * per);
     O.bB = (double*)take(sizeof(double) * per);
     double* gbT = (double*)take(sizeof(double) * per);
-    T* Sinv = (T*)take(sizeof(T) * n * B.nx);
+    T* Sinv = (T*)take(sizeof(T) * sinv_len(B.nx, B.ny, sizeof(T)));
     T* cys = (T*)take(sizeof(T) * n);
-    T* Sbuf = (T*)take(sizeof(T) * B.nx * B.nx);
     T* cxs = (T*)take(sizeof(T) * n);
-    T* zall = (T*)take(sizeof(T) * 32 * nw);
+    T* zall = (T*)take(sizeof(T) * 64 * nw);
     double* bsrc = basis ? nullptr : (double*)take(sizeof(double) * n);
     double* gcx = (double*)take(sizeof(double) * n);
     double* gcy = (double*)take(sizeof(double) * n);
@@ -419,7 +418,7 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
     for (int t = threadIdx.x; t < per; t += blockDim.x) gbT[t] = 0.0;
     build_ops(B, md, P, O);
     fill_scale(B, O, mixed);
-    factor_box<T, BW>(B, O, Sinv, cys, cxs, Sbuf, &flags[0]);
+    factor_box<T, BW, false>(B, O, Sinv, cys, cxs, &flags[0]);
     if (flags[0] && threadIdx.x == 0) {
         atomicOr(&P.status[0], ST_NOT_SPD);
         atomicExch(&P.status[2], job.item);
@@ -439,7 +438,7 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
     double* gTf = A.gTf + md.cell_off * 3;
     const double* gps = A.gps + (size_t)job.item * P.ncell_i_max;
     const double* gugi = A.gug + (size_t)job.item * MRCM_MAXSIDE * P.side_max;
-    T* zb = zall + warp * 32;
+    T* zb = zall + warp * 64;
     for (int k = warp; k < nrhs; k += nw) {
         // forward solution x_k
         int sk = -1, mk = 0;
@@ -644,10 +643,10 @@ size_t adj_smooth2d_smem(int prec, int nx, int ny) {
     const size_t n = (size_t)nx * ny;
     const size_t per = 2 * (size_t)(nx + ny);
     const size_t tsz = prec == 0 ? sizeof(double) : sizeof(float);
-    size_t s = align16(tsz * n * nx);
+    size_t s = align16(tsz * sinv_len(nx, ny, (int)tsz));
     s += align16(sizeof(double) * n) * 4 + align16(sizeof(double) * 2 * n);
     s += align16(sizeof(double) * per) * 3 + align16(sizeof(double) * n);
-    s += align16(tsz * n) + align16(tsz * 32) + align16(sizeof(double) * n) * 2;
+    s += align16(tsz * n) + align16(tsz * 64) + align16(sizeof(double) * n) * 2;
     if (prec != 0) s += align16(tsz * n);
     s += align16(sizeof(double) * 4 * n);
     return s + 64;

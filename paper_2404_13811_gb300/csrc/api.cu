@@ -21,6 +21,7 @@
 size_t local2d_smem(int prec, int nx, int ny, int nrhs, bool part);
 size_t smooth2d_smem(int prec, int nx, int ny);
 size_t spack_bytes(int prec, int nx, int ny);
+int local2d_class(int prec, int nx);
 cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int bw,
                            size_t smem, cudaStream_t s);
 cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems,
@@ -114,6 +115,7 @@ struct AdjWork {
 
 struct mrcm_handle {
     cudaStream_t stream = 0;
+    int device = 0;               // the device current at creation (all of the handle's memory lives there)
     mrcm_params prm{};
     int dim = 2;
     int count = 0;
@@ -464,7 +466,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         fac_stride = std::max(fac_stride, spack_bytes(prec, bx, by) / tsz);   // smoothing packs, 16-byte multiples
         dsc_stride = std::max(dsc_stride, (size_t)bx * by);
         auto add = [&](int type, int nx, int ny, int nrhs) {
-            int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
+            const int bw = local2d_class(prec, nx);
             byw[bw].push_back(Job{s, type});
             smem_w[bw] = std::max(smem_w[bw],
                                   local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1), type == JOB_PART));
@@ -493,6 +495,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     h->colour_off[1 << d] = (int)citems.size();
 
     // ---- device allocations ----
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(h, MRCM_ERR_CUDA, "no current CUDA device");
     int e = 0;
     const int nmem = (int)h->mem.size();
     if ((e = dalloc(h, &h->d_mem, nmem))) return e;
@@ -709,8 +712,9 @@ static int check_status(mrcm_handle* h) {
 
 // Internal accessors for the output path that lives with its static scratch (state.cu).
 int mrcm_internal_member_state(mrcm_handle* h, int member, cudaStream_t* st, const double** p, const double** u,
-                               long long* nc, int* nside, int* gauge) {
+                               long long* nc, int* nside, int* gauge, int* device) {
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "no solution yet");
+    *device = h->device;
     if (member < 0 || member >= (int)h->mem.size()) return fail(h, MRCM_ERR_BAD_INPUT, "bad member");
     const MemberDev& md = h->mem[member];
     *st = h->stream;

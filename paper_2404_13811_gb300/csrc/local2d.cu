@@ -27,7 +27,7 @@
 // ---------------------------------------------------------------------------
 // Steps 1, 2, 4 and 6 of Algorithm 1 for 2D subdomains.
 // ---------------------------------------------------------------------------
-template <typename T, int BW>
+template <typename T, int BW, bool EX>
 __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev Mth, const Job* jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool mixed = std::is_same<T, float>::value;
@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
     build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
-    factor_box<T, BW>(B, C.O, C.Sinv, C.cys, C.cxs, C.Sbuf, &C.flags[0]);
+    if (mixed) scale_ops(B, C.O);   // D A D: the factor and the refinement work in scaled variables
+    factor_box<T, BW, EX, mixed>(B, C.O, C.Sinv, C.cys, C.cxs, &C.flags[0]);
 
     // keep the factor for the smoothing steps, as the subdomain's smoothing pack
     const bool keep = (job.type == JOB_SFACT) || (job.type == JOB_BASIS && Mth.same_alpha);
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
         unsigned char* pk = (unsigned char*)((T*)P.fac + (size_t)job.item * P.fac_stride);
         const SPack L = spack_layout(B.nx, B.ny, sizeof(T));
         T* dst = (T*)pk;
-        const size_t nS = (size_t)B.n * B.nx;
+        const size_t nS = sinv_len(B.nx, B.ny, sizeof(T));
         for (size_t t = threadIdx.x; t < nS; t += blockDim.x) dst[t] = C.Sinv[t];
         double* dd = P.dsc + (size_t)job.item * P.dsc_stride;
         const double* fk = P.f + md.cell_off;
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
             ((double*)(pk + L.cx))[c] = C.O.cx[c];
             ((double*)(pk + L.cy))[c] = C.O.cy[c];
             ((double*)(pk + L.dsc))[c] = C.O.dsc[c];
-            ((double*)(pk + L.bst))[c] = source_rhs(B, C.O, fk, md.n[0], vk, md.h[1], md.h[0], nullptr, c % B.nx, c / B.nx);
+            ((double*)(pk + L.bst))[c] =
+                C.O.dsc[c] * source_rhs(B, C.O, fk, md.n[0], vk, md.h[1], md.h[0], nullptr, c % B.nx, c / B.nx);
             ((T*)(pk + L.cys))[c] = C.cys[c];
         }
         for (int t = threadIdx.x; t < 2 * (B.nx + B.ny); t += blockDim.x) {
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
     if (nrhs == 0) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* zb = C.zbuf + warp * 32;
+    T* zb = C.zbuf + warp * 64;
     const int npsi = Mth.npsi;
     const double vol = md.h[0] * md.h[1];
     const double ax = md.h[1], ay = md.h[0];
@@ -102,17 +104,43 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
                     if (q == 0) { sk = sid; break; }
                     --q;
                 }
-            RhsBasis rb{sk, mk};
-            it = warp_solve<T>(B, C.O, C.Sinv, C.cys, x, w, zb, rb, Mth.ir_tol, Mth.max_ir, &C.flags[1]);
+            if constexpr (mixed) {
+                // b~ on the Robin side: lane pos holds that of face pos
+                const int len = (sk >> 1) == 0 ? B.ny : B.nx;
+                double mine = 0.0;
+                if (lane < len) {
+                    const int ci = (sk >> 1) == 0 ? lane * B.nx + (sk == 0 ? 0 : B.nx - 1)
+                                                  : (sk == 2 ? 0 : (B.ny - 1) * B.nx) + lane;
+                    mine = C.O.dsc[ci] * C.O.bT[side_off(B, sk) + lane] * psi_val(mk, lane, len, B.rlen[sk]);
+                }
+                RhsScSide rb{sk, mine};
+                it = warp_solve_sc<RhsScSide, EX ? BW : 0>(B, C.O, C.Sinv, C.cys, x, w, zb, rb, Mth.ir_tol,
+                                                            Mth.max_ir, &C.flags[1]);
+            } else {
+                RhsBasis rb{sk, mk};
+                it = warp_solve<T, RhsBasis>(B, C.O, C.Sinv, C.cys, x, w, zb, rb, Mth.ir_tol, Mth.max_ir,
+                                             &C.flags[1]);
+            }
         } else {
-            // the particular problem: fixed right-hand side staged once
+            // the particular problem: fixed right-hand side staged once (b~ in the mixed form)
             for (int c = lane; c < B.n; c += 32) {
                 const int i = c % B.nx, j = c / B.nx;
-                C.bsrc[c] = source_rhs(B, C.O, fm, md.n[0], vol, ax, ay, nullptr, i, j);
+                C.bsrc[c] = C.O.dsc[c] * source_rhs(B, C.O, fm, md.n[0], vol, ax, ay, nullptr, i, j);
             }
             __syncwarp();
-            RhsStored rs{C.bsrc};
-            it = warp_solve<T>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol, Mth.max_ir, &C.flags[1]);
+            if constexpr (mixed) {
+                RhsScStored rs{C.bsrc};
+                it = warp_solve_sc<RhsScStored, EX ? BW : 0>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol,
+                                                              Mth.max_ir, &C.flags[1]);
+            } else {
+                RhsStored rs{C.bsrc};
+                it = warp_solve<T, RhsStored>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol, Mth.max_ir,
+                                              &C.flags[1]);
+            }
+        }
+        if constexpr (mixed) {
+            // back from the scaled iterate
+            for (int c = lane; c < B.n; c += 32) x[c] *= C.O.dsc[c];
         }
         maxit = max(maxit, it);
         nsolve += it;
@@ -144,14 +172,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
                 else        { i = offx + e; j = (sid == 2) ? offy : offy + nIy - 1; }
                 const int cL = j * B.nx + i;
                 const double pL = x[cL];
-                const double hkL = P.hk[(md.cell_off + (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j)) * 3 + a];
+                const long long gL = md.cell_off + (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
+                const double hkL = P.hk[gL * 3 + a];
+                // interior face transmissibility (unscaled) from the face coefficients
                 bool inner;
                 int cR;
                 double Tf;
-                if (sid == 0) { inner = i > 0; cR = cL - 1; Tf = inner ? C.O.cx[cL - 1] : 0; }
-                else if (sid == 1) { inner = i < B.nx - 1; cR = cL + 1; Tf = inner ? C.O.cx[cL] : 0; }
-                else if (sid == 2) { inner = j > 0; cR = cL - B.nx; Tf = inner ? C.O.cy[cL - B.nx] : 0; }
-                else { inner = j < B.ny - 1; cR = cL + B.nx; Tf = inner ? C.O.cy[cL] : 0; }
+                if (sid == 0) { inner = i > 0; cR = cL - 1; Tf = inner ? P.Tf[(gL - 1) * 3 + 0] : 0; }
+                else if (sid == 1) { inner = i < B.nx - 1; cR = cL + 1; Tf = inner ? P.Tf[gL * 3 + 0] : 0; }
+                else if (sid == 2) { inner = j > 0; cR = cL - B.nx; Tf = inner ? P.Tf[(gL - md.n[0]) * 3 + 1] : 0; }
+                else { inner = j < B.ny - 1; cR = cL + B.nx; Tf = inner ? P.Tf[gL * 3 + 1] : 0; }
                 double uo, pi;
                 if (inner) {
                     uo = Tf * (pL - x[cR]) * rarea;
@@ -267,6 +297,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         }
     }
     // mixed form: the refinement starts from the current pressure on the box
+    // (read now; scaled once the pack, with D, has arrived)
     if (mixed)
         for (int c = threadIdx.x; c < B.n; c += blockDim.x)
             x[c] = pst[(B.lo[0] + c % B.nx) + (long long)md.n[0] * (B.lo[1] + c / B.nx)];
@@ -289,12 +320,24 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
             for (int pos = threadIdx.x; pos < len; pos += blockDim.x) {
                 const int i = a == 0 ? ((sid == 0) ? 0 : B.nx - 1) : pos;
                 const int j = a == 0 ? pos : ((sid == 2) ? 0 : B.ny - 1);
-                bsrc[j * B.nx + i] += O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos];
+                const int c = j * B.nx + i;
+                bsrc[c] += O.dsc[c] * (O.bT[side_off(B, sid) + pos] * lam[side_off(B, sid) + pos]);
             }
             __syncthreads();
         }
-        RhsStored rs{bsrc};
-        it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0], mixed);
+        if constexpr (mixed) {
+            // the scaled start x~ = D^-1 x (an FP32 reciprocal of the FP32 scale: a start only)
+            for (int c = threadIdx.x; c < B.n; c += blockDim.x)
+                x[c] *= f2d_bits(__frcp_rn(d2f_bits(O.dsc[c])));
+            __syncthreads();
+            it = cta_solve_sc(B, O, (const float*)Sinv, (const float*)cys, x, (float*)w, (float*)zbuf, nrm, bsrc,
+                              Mth.ir_tol, Mth.max_ir, &flags[0], true);
+            for (int c = threadIdx.x; c < B.n; c += blockDim.x) x[c] *= O.dsc[c];
+            __syncthreads();
+        } else {
+            RhsStored rs{bsrc};
+            it = cta_solve<T>(B, O, Sinv, cys, x, w, zbuf, red, nrm, rs, Mth.ir_tol, Mth.max_ir, &flags[0], false);
+        }
     } else if (threadIdx.x == 0) {
         flags[1] = 1;
     }
@@ -314,6 +357,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     const int offx = sd.lo[0] - B.lo[0], offy = sd.lo[1] - B.lo[1];
     double* pw = P.p + md.cell_off;
     double* uw = P.u + md.cell_off * 4;
+    const double* Tfg = P.Tf + md.cell_off * 3;
     const double rax = 1.0 / md.h[1], ray = 1.0 / md.h[0];
     for (int c = threadIdx.x; c < nIx * nIy; c += blockDim.x) {
         const int i = c % nIx + offx, j = c / nIx + offy;
@@ -329,7 +373,9 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
                               (sid == 3 && j == B.ny - 1);
             if (!edge) {
                 const int cn = sid == 0 ? cl - 1 : sid == 1 ? cl + 1 : sid == 2 ? cl - B.nx : cl + B.nx;
-                const double Tf = sid == 0 ? O.cx[cl - 1] : sid == 1 ? O.cx[cl] : sid == 2 ? O.cy[cl - B.nx] : O.cy[cl];
+                // the unscaled face transmissibility from the face coefficients (shared memory holds D A D)
+                const double Tf = sid == 0 ? Tfg[(g - 1) * 3 + 0] : sid == 1 ? Tfg[g * 3 + 0]
+                                : sid == 2 ? Tfg[(g - md.n[0]) * 3 + 1] : Tfg[g * 3 + 1];
                 uo[sid] = Tf * (pc - x[cn]) * rarea;
             } else {
                 const int pos = a == 0 ? j : i;
@@ -370,10 +416,10 @@ size_t smooth2d_smem(int prec, int nx, int ny) {
     return s + 64;
 }
 
-template <typename T, int BW>
+template <typename T, int BW, bool EX>
 static cudaError_t launch_local_t(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs,
                                   size_t smem, cudaStream_t s) {
-    auto kern = k_local2d<T, BW>;
+    auto kern = k_local2d<T, BW, EX>;
     static size_t set_smem = 0;
     if (smem > set_smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -387,20 +433,39 @@ static cudaError_t launch_local_t(const DevPtrs& P, const MethodDev& M, const Jo
     return cudaGetLastError();
 }
 
-cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int bw,
+// Job classes: local2d_class(prec, nx).  The FP32 form has one kernel per line
+// width that is a multiple of 4 (width known at compile time: its line
+// inversions and sweeps run without width guards); other widths, and the
+// FP64 form, run a kernel for widths up to 8, 16, 24 or 32.
+int local2d_class(int prec, int nx) {
+    if (prec != 0 && nx % 4 == 0 && nx <= 32) return nx;
+    return 100 + (nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32);
+}
+
+cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs, int njobs, int cls,
                            size_t smem, cudaStream_t s) {
     if (njobs == 0) return cudaSuccess;
     if (M.prec == 0) {
-        if (bw <= 8) return launch_local_t<double, 8>(P, M, jobs, njobs, smem, s);
-        if (bw <= 16) return launch_local_t<double, 16>(P, M, jobs, njobs, smem, s);
-        if (bw <= 24) return launch_local_t<double, 24>(P, M, jobs, njobs, smem, s);
-        return launch_local_t<double, 32>(P, M, jobs, njobs, smem, s);
-    } else {
-        if (bw <= 8) return launch_local_t<float, 8>(P, M, jobs, njobs, smem, s);
-        if (bw <= 16) return launch_local_t<float, 16>(P, M, jobs, njobs, smem, s);
-        if (bw <= 24) return launch_local_t<float, 24>(P, M, jobs, njobs, smem, s);
-        return launch_local_t<float, 32>(P, M, jobs, njobs, smem, s);
+        if (cls <= 108) return launch_local_t<double, 8, false>(P, M, jobs, njobs, smem, s);
+        if (cls <= 116) return launch_local_t<double, 16, false>(P, M, jobs, njobs, smem, s);
+        if (cls <= 124) return launch_local_t<double, 24, false>(P, M, jobs, njobs, smem, s);
+        return launch_local_t<double, 32, false>(P, M, jobs, njobs, smem, s);
     }
+    switch (cls) {
+        case 4: return launch_local_t<float, 4, true>(P, M, jobs, njobs, smem, s);
+        case 8: return launch_local_t<float, 8, true>(P, M, jobs, njobs, smem, s);
+        case 12: return launch_local_t<float, 12, true>(P, M, jobs, njobs, smem, s);
+        case 16: return launch_local_t<float, 16, true>(P, M, jobs, njobs, smem, s);
+        case 20: return launch_local_t<float, 20, true>(P, M, jobs, njobs, smem, s);
+        case 24: return launch_local_t<float, 24, true>(P, M, jobs, njobs, smem, s);
+        case 28: return launch_local_t<float, 28, true>(P, M, jobs, njobs, smem, s);
+        case 32: return launch_local_t<float, 32, true>(P, M, jobs, njobs, smem, s);
+        default: break;
+    }
+    if (cls <= 108) return launch_local_t<float, 8, false>(P, M, jobs, njobs, smem, s);
+    if (cls <= 116) return launch_local_t<float, 16, false>(P, M, jobs, njobs, smem, s);
+    if (cls <= 124) return launch_local_t<float, 24, false>(P, M, jobs, njobs, smem, s);
+    return launch_local_t<float, 32, false>(P, M, jobs, njobs, smem, s);
 }
 
 cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,

@@ -208,7 +208,7 @@ __global__ void k_output_static(const double* __restrict__ p, const double* __re
 
 // internal accessors defined with the handle (api.cu)
 int mrcm_internal_member_state(mrcm_handle* h, int member, cudaStream_t* st, const double** p, const double** u,
-                               long long* nc, int* nside, int* gauge);
+                               long long* nc, int* nside, int* gauge, int* device);
 int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg);
 
 static double* g_partials_addr[MRCM_STATIC_MAX_DEVICES] = {nullptr};
@@ -218,8 +218,8 @@ extern "C" int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellface
     cudaStream_t st;
     const double *p, *u;
     long long nc;
-    int nside, gauge;
-    int rc = mrcm_internal_member_state(h, member, &st, &p, &u, &nc, &nside, &gauge);
+    int nside, gauge, hdev;
+    int rc = mrcm_internal_member_state(h, member, &st, &p, &u, &nc, &nside, &gauge, &hdev);
     if (rc) return rc;
     if (nc > MRCM_STATIC_MAX_CELLS)
         return mrcm_internal_fail(h, MRCM_ERR_UNSUPPORTED,
@@ -228,8 +228,14 @@ extern "C" int mrcm_fluxes_static(mrcm_handle* h, int member, double* u_cellface
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= MRCM_STATIC_MAX_DEVICES)
         return mrcm_internal_fail(h, MRCM_ERR_CUDA, "mrcm_fluxes_static: no usable current device");
+    // the address below belongs to the current device, the kernels run on the
+    // handle's stream: both must be the handle's device
+    if (dev != hdev)
+        return mrcm_internal_fail(h, MRCM_ERR_BAD_INPUT,
+                                  "mrcm_fluxes_static: the handle's device must be the current device");
     if (!g_partials_addr[dev]) {
-        // once per device, with that device current: the device address of the static array
+        // once per device, with that device current: the device address of the
+        // static array (every thread that races here stores the same value)
         void* addr = nullptr;
         e = cudaGetSymbolAddress(&addr, g_gauge_partials);
         if (e != cudaSuccess) return mrcm_internal_fail(h, MRCM_ERR_CUDA, cudaGetErrorString(e));

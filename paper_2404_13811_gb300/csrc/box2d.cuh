@@ -263,9 +263,11 @@ __device__ __forceinline__ void gj_regs(T (&a)[BW], int b, int* bad) {
 // i): T_j minus C S^-1 C for each kept neighbour inverse given (up: the
 // inverse of line j - 1, coupled through cys_{j-1}; dn: the inverse of line
 // j + 1, coupled through cys_j).  Off-diagonal entries in T, the diagonal
-// d_i - sum c_i^2 (S^-1)_ii -- where the cancellation is -- in FP64.  The
-// neighbour inverses are read by column (lane i reads entry (c, i) of the
-// symmetric block: consecutive lanes, consecutive words).
+// d_i - sum c_i^2 (S^-1)_ii -- where the cancellation is -- in FP64.  With
+// the width known at compile time (EX, FP32) lane i reads row i of the
+// (symmetric) neighbour inverse and the coupling vector as float4 and the
+// FP64 diagonal converts on the integer pipe (FP32 -> FP64 exact, the FP64
+// result truncated to FP32 within one ulp); otherwise lane i reads column i.
 template <typename T, int BW, bool EX, bool SC>
 __device__ __forceinline__ void form_line(T (&a)[BW], const Ops& O, const T* cys, const T* cxs, int b, int ld,
                                           int j, const T* up, const T* dn) {
@@ -279,20 +281,68 @@ __device__ __forceinline__ void form_line(T (&a)[BW], const Ops& O, const T* cys
     const int ci = j * b + ii;
     const T cu = up ? cys[ci - b] : T(0);
     const T cn = dn ? cys[ci] : T(0);
+    // in-line couplings of cell i: to i + 1 and to i - 1
+    const T xr = (act && ii < b - 1) ? cxs[ci] : T(0);
+    const T xl = (act && ii > 0) ? cxs[ci - 1] : T(0);
+    constexpr bool VEC = EX && std::is_same<T, float>::value && (BW % 4 == 0);
     double d = SC ? O.cd[ci] : O.cd[ci] * O.dsc[ci] * O.dsc[ci];
-    if (up) d -= (double)cu * (double)cu * (double)up[ii * ld + ii];
-    if (dn) d -= (double)cn * (double)cn * (double)dn[ii * ld + ii];
-    const T dT = (T)d;
+    if constexpr (VEC) {
+        const double cu2 = up ? f2d_bits(cu) * f2d_bits(cu) : 0.0;   // exact in FP64
+        const double cn2 = dn ? f2d_bits(cn) * f2d_bits(cn) : 0.0;
+        if (up) d = fma(-cu2, f2d_bits(up[ii * ld + ii]), d);
+        if (dn) d = fma(-cn2, f2d_bits(dn[ii * ld + ii]), d);
+    } else {
+        if (up) d -= (double)cu * (double)cu * (double)up[ii * ld + ii];
+        if (dn) d -= (double)cn * (double)cn * (double)dn[ii * ld + ii];
+    }
+    T dT;
+    if constexpr (VEC) dT = d2f_bits(d);
+    else dT = (T)d;
+    if constexpr (VEC) {
+        constexpr int NQ = BW / 4;
+        float4 ru[NQ], rd[NQ], ku[NQ], kd[NQ];
+        if (up) {
+            const float4* r = reinterpret_cast<const float4*>(up + ii * ld);
+            const float4* k = reinterpret_cast<const float4*>(cys + (j - 1) * b);
 #pragma unroll
-    for (int c = 0; c < BW; ++c) {
-        T s = T(0);
-        if (act && (EX || c < b)) {
-            if (c == i + 1) s = cxs[ci];
-            else if (c == i - 1) s = cxs[j * b + c];
-            if (up) s -= cu * up[c * ld + i] * cys[(j - 1) * b + c];
-            if (dn) s -= cn * dn[c * ld + i] * cys[j * b + c];
+            for (int q = 0; q < NQ; ++q) { ru[q] = r[q]; ku[q] = k[q]; }
         }
-        a[c] = (act && (EX || c < b)) ? (c == i ? dT : s) : T(i == c ? 1 : 0);
+        if (dn) {
+            const float4* r = reinterpret_cast<const float4*>(dn + ii * ld);
+            const float4* k = reinterpret_cast<const float4*>(cys + j * b);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) { rd[q] = r[q]; kd[q] = k[q]; }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float su[4] = {0.f, 0.f, 0.f, 0.f}, sd[4] = {0.f, 0.f, 0.f, 0.f};
+            if (up) {
+                su[0] = cu * ru[q].x * ku[q].x; su[1] = cu * ru[q].y * ku[q].y;
+                su[2] = cu * ru[q].z * ku[q].z; su[3] = cu * ru[q].w * ku[q].w;
+            }
+            if (dn) {
+                sd[0] = cn * rd[q].x * kd[q].x; sd[1] = cn * rd[q].y * kd[q].y;
+                sd[2] = cn * rd[q].z * kd[q].z; sd[3] = cn * rd[q].w * kd[q].w;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = 4 * q + e;
+                const float off = (c == i + 1 ? xr : c == i - 1 ? xl : 0.f) - su[e] - sd[e];
+                a[c] = act ? (c == i ? dT : off) : T(i == c ? 1 : 0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < BW; ++c) {
+            T s = T(0);
+            if (act && (EX || c < b)) {
+                s = c == i + 1 ? xr : c == i - 1 ? xl : T(0);
+                // by column (consecutive lanes, consecutive words) where rows are not read as float4
+                if (up) s -= cu * up[c * ld + ii] * cys[(j - 1) * b + c];
+                if (dn) s -= cn * dn[c * ld + ii] * cys[j * b + c];
+            }
+            a[c] = (act && (EX || c < b)) ? (c == i ? dT : s) : T(i == c ? 1 : 0);
+        }
     }
 }
 

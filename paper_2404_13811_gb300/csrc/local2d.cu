@@ -301,6 +301,23 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     if (mixed)
         for (int c = threadIdx.x; c < B.n; c += blockDim.x)
             x[c] = pst[(B.lo[0] + c % B.nx) + (long long)md.n[0] * (B.lo[1] + c / B.nx)];
+    // the unscaled face transmissibilities the output needs (shared memory holds D A D), read while the pack
+    // is in flight: this thread's cells of Omega_i, faces x-, x+, y-, y+ (two cells per thread at most)
+    const int nIx = sd.hi[0] - sd.lo[0], nIy = sd.hi[1] - sd.lo[1];
+    const int offx = sd.lo[0] - B.lo[0], offy = sd.lo[1] - B.lo[1];
+    const double* Tfg = P.Tf + md.cell_off * 3;
+    double tfo[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int c = threadIdx.x + q * blockDim.x;
+        const int i = c % nIx + offx, j = c / nIx + offy;
+        const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
+        const bool ok = c < nIx * nIy;
+        tfo[q][0] = (ok && i > 0) ? Tfg[(g - 1) * 3 + 0] : 0.0;
+        tfo[q][1] = (ok && i < B.nx - 1) ? Tfg[g * 3 + 0] : 0.0;
+        tfo[q][2] = (ok && j > 0) ? Tfg[(g - md.n[0]) * 3 + 1] : 0.0;
+        tfo[q][3] = (ok && j < B.ny - 1) ? Tfg[g * 3 + 1] : 0.0;
+    }
     int it = 0;
     // every thread reads the staged pack: all wait for the copy, and agree on a late one
     const bool arrived = mbar_wait(&bar, 0);
@@ -353,18 +370,26 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         return;
     }
     // overwrite (u, p) on Omega_i with the restriction
-    const int nIx = sd.hi[0] - sd.lo[0], nIy = sd.hi[1] - sd.lo[1];
-    const int offx = sd.lo[0] - B.lo[0], offy = sd.lo[1] - B.lo[1];
     double* pw = P.p + md.cell_off;
     double* uw = P.u + md.cell_off * 4;
-    const double* Tfg = P.Tf + md.cell_off * 3;
     const double rax = 1.0 / md.h[1], ray = 1.0 / md.h[0];
-    for (int c = threadIdx.x; c < nIx * nIy; c += blockDim.x) {
+    for (int q = 0, c = threadIdx.x; c < nIx * nIy; ++q, c += blockDim.x) {
         const int i = c % nIx + offx, j = c / nIx + offy;
         const int cl = j * B.nx + i;
         const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
         const double pc = x[cl];
         pw[g] = pc;
+        // transmissibilities: prefetched for a thread's first two cells, else read here
+        double tf[4];
+        if (q < 2) {
+#pragma unroll
+            for (int sid = 0; sid < 4; ++sid) tf[sid] = q == 0 ? tfo[0][sid] : tfo[1][sid];
+        } else {
+            tf[0] = i > 0 ? Tfg[(g - 1) * 3 + 0] : 0.0;
+            tf[1] = i < B.nx - 1 ? Tfg[g * 3 + 0] : 0.0;
+            tf[2] = j > 0 ? Tfg[(g - md.n[0]) * 3 + 1] : 0.0;
+            tf[3] = j < B.ny - 1 ? Tfg[g * 3 + 1] : 0.0;
+        }
         double uo[4];
         for (int sid = 0; sid < 4; ++sid) {
             const int a = sid >> 1;
@@ -373,10 +398,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
                               (sid == 3 && j == B.ny - 1);
             if (!edge) {
                 const int cn = sid == 0 ? cl - 1 : sid == 1 ? cl + 1 : sid == 2 ? cl - B.nx : cl + B.nx;
-                // the unscaled face transmissibility from the face coefficients (shared memory holds D A D)
-                const double Tf = sid == 0 ? Tfg[(g - 1) * 3 + 0] : sid == 1 ? Tfg[g * 3 + 0]
-                                : sid == 2 ? Tfg[(g - md.n[0]) * 3 + 1] : Tfg[g * 3 + 1];
-                uo[sid] = Tf * (pc - x[cn]) * rarea;
+                uo[sid] = tf[sid] * (pc - x[cn]) * rarea;
             } else {
                 const int pos = a == 0 ? j : i;
                 const double Tb = O.bT[side_off(B, sid) + pos];

@@ -91,7 +91,8 @@ typedef struct {
  *   precision    MRCM_FP64 or MRCM_MIXED.
  *   ir_tol       relative residual (inf-norm; Jacobi-scaled for the local
  *                solves) that refinement must reach (mixed local solves and
- *                the interface solve).  3D local solves refine on to their
+ *                the interface solve; the FP64 form refines its interface
+ *                solve on to 1e-2 ir_tol).  3D local solves refine on to their
  *                residual floor: they stop at 1e-3 ir_tol, or below ir_tol
  *                once the residual no longer halves per step.
  *   max_ir       maximum refinement steps. */
@@ -237,8 +238,28 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
 /* Counters of the last calls: ints[0] = number of subdomains (all members),
  * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
  * last solve, ints[3] = largest local refinement count of the last
- * build/smooth call, ints[4] = local solves performed so far;
- * dbl[0] = last interface relative residual.  Either pointer may be NULL. */
+ * build/smooth call, ints[4] = local solves performed so far, ints[5] = the
+ * slab inverses of the interface reduction (0 Gauss-Jordan, 1 LU: chosen per
+ * handle by the autotuner below), ints[6] = 1 when the last interface solve
+ * needed the GMRES fallback, ints[7] = where the slab-inverse choice came from
+ * (0 not made or not a choice: slabs larger than 256 unknowns always use the
+ * LU; 1 the tuning cache; 2 measured on this handle's first interface solve);
+ * dbl[0] = last interface relative residual, dbl[1] / dbl[2] = the measured
+ * device ms of the Gauss-Jordan / LU variant (factorisation + refinement to
+ * ir_tol; 0 when not measured).  Either pointer may be NULL; at most nints /
+ * ndbl entries are written.
+ *
+ * Autotuner.  The slab inverses of the interface reduction are computed by
+ * blocked Gauss-Jordan elimination (one pass, for slabs of at most 256
+ * unknowns) or by an LU factorisation followed by the inverse columns.  The
+ * first mrcm_solve_interface of a handle (and the first after
+ * mrcm_set_permeability) times both -- device time of the factorisation and
+ * of the refinement steps it needs -- and keeps the faster one that reaches
+ * ir_tol; a later refinement that stalls with Gauss-Jordan switches the handle
+ * to the LU.  With the environment variable MRCM_TUNE_CACHE naming a JSON file,
+ * the choice is read from it by shape class (dimension, slab size, slab and
+ * level counts, members, precision, space, ir_tol) when present and written to
+ * it after a measurement. */
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl);
 
 /* Device-time profiling of the calls above.  enable = 1 starts recording a

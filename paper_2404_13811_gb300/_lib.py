@@ -231,11 +231,14 @@ def mrcm_backward(h, dL_du, dL_dp, dL_dlogK):
 
 def mrcm_stats(h):
     lib = load()
-    ints = (C.c_int * 5)()
-    dbl = (C.c_double * 1)()
-    _check(lib, h, lib.mrcm_stats(h, ints, 5, dbl, 1))
+    ints = (C.c_int * 8)()
+    dbl = (C.c_double * 3)()
+    _check(lib, h, lib.mrcm_stats(h, ints, 8, dbl, 3))
     return {"subdomains": ints[0], "interface_unknowns": ints[1], "interface_ir_steps": ints[2],
-            "local_ir_steps": ints[3], "local_solves": ints[4], "interface_residual": dbl[0]}
+            "local_ir_steps": ints[3], "local_solves": ints[4],
+            "slab_inverse": "gauss-jordan" if ints[5] == 0 else "lu", "interface_gmres": bool(ints[6]),
+            "slab_inverse_source": {0: "fixed", 1: "cache", 2: "measured"}.get(ints[7], ints[7]),
+            "interface_residual": dbl[0], "tune_ms": {"gauss-jordan": dbl[1], "lu": dbl[2]}}
 
 
 def mrcm_profile(h, enable):

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <vector>
@@ -47,7 +48,8 @@ cudaError_t kry_from_bq(const IfPtrs& I, double* z, int n, cudaStream_t s);
 cudaError_t kry_axpby(double* y, const double* x, double a, double b, int n, cudaStream_t s);
 cudaError_t kry_dot(const double* a, const double* b, int n, double* part, cudaStream_t s);
 int kry_blocks();
-cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
+cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, int variant, cudaStream_t s);
+int slab_inverse_gj_ok(int npad);
 size_t elim_smem_bytes(int nmv, int cw);
 size_t lu_smem(int np, int xch);
 size_t local3d_smem(int prec, int nx, int ny, int nz, bool part);
@@ -173,6 +175,9 @@ struct mrcm_handle {
     int if_iters = 0;
     double if_res = 0.0;
     bool if_krylov = false;       // the last interface solve needed the GMRES fallback
+    int slab_variant = -1;        // slab inverses: -1 not chosen yet, 0 Gauss-Jordan, 1 LU (autotuner)
+    int tune_source = 0;          // 0 none, 1 from the tuning cache, 2 measured by this handle
+    double tune_ms[2] = {0.0, 0.0};   // measured device ms (factor + refine) of Gauss-Jordan / LU
     double* d_kry = nullptr;      // its workspace (allocated on first use)
     int loc_ir = 0;
     long long local_solves = 0;
@@ -755,7 +760,7 @@ static int issue_interface_factor(mrcm_handle* h) {
         if (L.count == 0) continue;
         {
             Phase lu(h, 6);
-            CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, st));
+            CUDA_TRY(h, lu_inverse(I, h->d_elims + L.off, L.count, h->d_status, h->slab_variant, st));
         }
         h->launches[1] += 1;
         h->launches[6] += 1;
@@ -1104,55 +1109,236 @@ static int krylov_interface(mrcm_handle* h, double* worst_out) {
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Interface factorisation + stationary FP64 refinement, and the autotuner of
+// the slab inverses.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Device time of the kernels issued between start() and stop() (events on
+// the handle's stream), summed over segments.
+struct DevTimer {
+    mrcm_handle* h;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> seg;
+    cudaEvent_t a = nullptr;
+    explicit DevTimer(mrcm_handle* hh) : h(hh) {}
+    void start() {
+        if (cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, h->stream);
+    }
+    void stop() {
+        cudaEvent_t b = nullptr;
+        if (a && cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, h->stream);
+            seg.push_back({a, b});
+        }
+        a = nullptr;
+    }
+    double ms() {
+        double t = 0.0;
+        cudaStreamSynchronize(h->stream);
+        for (auto& q : seg) {
+            float f = 0.f;
+            if (cudaEventElapsedTime(&f, q.first, q.second) == cudaSuccess) t += f;
+        }
+        return t;
+    }
+    ~DevTimer() {
+        for (auto& q : seg) {
+            cudaEventDestroy(q.first);
+            cudaEventDestroy(q.second);
+        }
+        if (a) cudaEventDestroy(a);
+    }
+};
+
+struct RefineOut {
+    int it = 0;
+    double worst = 0.0;
+    bool stalled = false;
+    double ms = 0.0;   // device time of the factorisation and the refinement steps
+};
+
+}  // namespace
+
+// One factorisation with the handle's slab inverses and the refinement from
+// X = 0 (residual read back after every step; stops at ir_tol, at the step
+// limit, or when a step no longer reduces the residual below 0.9 of the
+// previous one: then the FP32 factors are too poor a preconditioner for
+// stationary refinement of this system).
+// The interface refinement's target: ir_tol, in the FP64 form 1e-2 ir_tol
+// (that form is the full-FP64 reference of the method, so its interface
+// solve goes on towards the FP64 residual floor).
+static double if_target(const mrcm_handle* h) {
+    return h->prm.precision == MRCM_FP64 ? 1e-2 * h->mth.ir_tol : h->mth.ir_tol;
+}
+
+static int factor_refine(mrcm_handle* h, RefineOut* o, std::string* hist) {
+    DevTimer tm(h);
+    tm.start();
+    int rc = issue_interface_factor(h);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    const int max_it = std::max(8, h->prm.max_ir);
+    CUDA_TRY(h, cudaMemsetAsync(h->I.x, 0, sizeof(double) * h->nif, st));
+    double prev = 0.0;
+    o->stalled = false;
+    o->worst = 0.0;
+    int it = 0;
+    for (;; ++it) {
+        rc = issue_residual(h);
+        if (rc) return rc;
+        tm.stop();
+        if (it > 0) {
+            rc = read_if_residual(h, &o->worst);
+            if (rc) return rc;
+            char buf[32];
+            snprintf(buf, sizeof(buf), " %.2e", o->worst);
+            *hist += buf;
+            if (!std::isfinite(o->worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
+            if (o->worst <= if_target(h) || it >= max_it) break;
+            if (it >= 2 && o->worst > 0.9 * prev) {
+                o->stalled = true;
+                break;
+            }
+            prev = o->worst;
+        }
+        tm.start();
+        rc = issue_if_sweeps(h);
+        if (rc) return rc;
+    }
+    o->it = it;
+    o->ms = tm.ms();
+    return 0;
+}
+
+// The autotuner's cache (environment MRCM_TUNE_CACHE = a JSON file): one
+// object per shape class of the interface reduction, keyed by tune_key,
+// holding the chosen slab inverses and the measured device times of both
+// variants (factorisation + refinement to ir_tol).
+static std::string tune_key(const mrcm_handle* h) {
+    char buf[192];
+    snprintf(buf, sizeof(buf), "interface dim%d npad%d slabs%zu levels%zu members%zu prec%d space%d tol%.0e", h->dim,
+             h->npad, h->slabs.size(), h->levels.size(), h->mem.size(), h->prm.precision, h->prm.space,
+             h->mth.ir_tol);
+    return buf;
+}
+
+static int tune_cache_lookup(const std::string& key) {
+    const char* path = std::getenv("MRCM_TUNE_CACHE");
+    if (!path || !*path) return -1;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return -1;
+    char line[512];
+    int v = -1;
+    const std::string tag = "\"" + key + "\": {\"slab_inverse\": \"";
+    while (std::fgets(line, sizeof(line), f)) {
+        const char* q = std::strstr(line, tag.c_str());
+        if (!q) continue;
+        q += tag.size();
+        v = std::strncmp(q, "lu", 2) == 0 ? 1 : std::strncmp(q, "gauss-jordan", 12) == 0 ? 0 : -1;
+    }
+    std::fclose(f);
+    return v;
+}
+
+static void tune_cache_store(const std::string& key, int variant, double ms_gj, double ms_lu, int it_gj, int it_lu) {
+    const char* path = std::getenv("MRCM_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::vector<std::string> keep;
+    const std::string tag = "\"" + key + "\": ";
+    if (FILE* f = std::fopen(path, "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof(line), f)) {
+            std::string l(line);
+            while (!l.empty() && (l.back() == '\n' || l.back() == ',' || l.back() == ' ')) l.pop_back();
+            if (l.size() < 3 || l[0] == '{' || l[0] == '}' || l.find(tag) != std::string::npos) continue;
+            keep.push_back(l);
+        }
+        std::fclose(f);
+    }
+    char buf[512];
+    snprintf(buf, sizeof(buf),
+             "  \"%s\": {\"slab_inverse\": \"%s\", \"gauss_jordan_ms\": %.4f, \"gauss_jordan_steps\": %d, "
+             "\"lu_ms\": %.4f, \"lu_steps\": %d}",
+             key.c_str(), variant == 0 ? "gauss-jordan" : "lu", ms_gj, it_gj, ms_lu, it_lu);
+    keep.push_back(buf);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    for (size_t i = 0; i < keep.size(); ++i) std::fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename(tmp.c_str(), path);
+}
+
 int mrcm_solve_interface(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_BASIS) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must follow mrcm_build_basis");
     h->err.clear();
-    int rc = issue_interface_factor(h);
-    if (rc) return rc;
-    // refinement, convergence read back after every step
-    cudaStream_t st = h->stream;
-    const int nmem = (int)h->mem.size();
-    int it = 0;
-    double worst = 0.0;
     std::string hist;
-    const int max_it = std::max(8, h->prm.max_ir);
-    CUDA_TRY(h, cudaMemsetAsync(h->I.x, 0, sizeof(double) * h->nif, st));
-    double prev = 0.0;
-    bool stalled = false;
-    for (;; ++it) {
-        rc = issue_residual(h);
-        if (rc) return rc;
-        if (it > 0) {
-            rc = read_if_residual(h, &worst);
-            if (rc) return rc;
-            char buf[32];
-            snprintf(buf, sizeof(buf), " %.2e", worst);
-            hist += buf;
-            if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface refinement diverged");
-            if (worst <= h->mth.ir_tol || it >= max_it) break;
-            // no longer contracting: the FP32 factor is too poor a preconditioner
-            // for stationary refinement of this system; GMRES takes over
-            if (it >= 2 && worst > 0.9 * prev) {
-                stalled = true;
-                break;
+    RefineOut o;
+    int rc = 0;
+    const bool gj_ok = slab_inverse_gj_ok(h->npad);
+    if (!gj_ok) h->slab_variant = 1;
+    if (h->slab_variant < 0) {
+        // autotuner: the cached choice for this shape class, else both slab
+        // inverses timed on this solve (device time of the factorisation and
+        // the refinement steps) and the faster one that converges kept
+        const std::string key = tune_key(h);
+        const int cached = tune_cache_lookup(key);
+        if (cached >= 0) {
+            h->slab_variant = cached;
+            h->tune_source = 1;
+        } else {
+            RefineOut a, b;
+            h->slab_variant = 0;
+            hist += " [gauss-jordan]";
+            if ((rc = factor_refine(h, &a, &hist))) return rc;
+            const bool a_ok = a.worst <= if_target(h);
+            h->slab_variant = 1;
+            hist += " [lu]";
+            if ((rc = factor_refine(h, &b, &hist))) return rc;
+            const bool b_ok = b.worst <= if_target(h);
+            const int choice = (a_ok && (!b_ok || a.ms < b.ms)) ? 0 : 1;
+            h->tune_ms[0] = a.ms;
+            h->tune_ms[1] = b.ms;
+            h->tune_source = 2;
+            tune_cache_store(key, choice, a.ms, b.ms, a.it, b.it);
+            h->slab_variant = choice;
+            if (choice == 0) {
+                // the handle's state is the LU run's: solve again with the choice
+                hist += " [gauss-jordan]";
+                if ((rc = factor_refine(h, &o, &hist))) return rc;
+            } else {
+                o = b;
             }
-            prev = worst;
         }
-        rc = issue_if_sweeps(h);
-        if (rc) return rc;
     }
-    (void)nmem;
+    if (o.it == 0) {   // not solved by the tuning runs of this call
+        if ((rc = factor_refine(h, &o, &hist))) return rc;
+    }
     h->if_krylov = false;
-    if (worst > h->mth.ir_tol && (stalled || it >= max_it)) {
+    const int max_it = std::max(8, h->prm.max_ir);
+    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it) && h->slab_variant == 0) {
+        // the Gauss-Jordan slab inverses are the less accurate preconditioner on
+        // very ill-conditioned interface systems: refactor with the slab LU and
+        // refine again (the handle keeps the LU for its later solves and captures)
+        h->slab_variant = 1;
+        hist += " (slab LU)";
+        if ((rc = factor_refine(h, &o, &hist))) return rc;
+    }
+    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it)) {
+        double worst = o.worst;
         rc = krylov_interface(h, &worst);
         if (rc) return rc;
+        o.worst = worst;
         h->if_krylov = true;
         hist += " (GMRES)";
     }
-    h->if_iters = it;
-    h->if_res = worst;
-    if (worst > h->mth.ir_tol * 1e3)
+    h->if_iters = o.it;
+    h->if_res = o.worst;
+    if (o.worst > h->mth.ir_tol * 1e3)
         return fail(h, MRCM_ERR_NO_CONVERGENCE, "interface refinement stalled; residuals:" + hist);
     rc = issue_assemble(h);
     if (rc) return rc;
@@ -1313,6 +1499,8 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
     CUDA_TRY(h, cudaStreamSynchronize(st));
     h->stage = ST_CREATED;
     h->if_iters = 0;  // a captured step re-learns its refinement count
+    h->slab_variant = -1;   // and the new operator its slab inverses (autotuner)
+    h->tune_source = 0;
     if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
@@ -1420,9 +1608,11 @@ int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_l
 
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl) {
     if (!h) return MRCM_ERR_BAD_INPUT;
-    long long vals[5] = {(long long)h->sub.size(), h->nif, h->if_iters, h->loc_ir, h->local_solves};
-    for (int i = 0; i < nints && i < 5; ++i) ints[i] = (int)vals[i];
-    if (dbl && ndbl > 0) dbl[0] = h->if_res;
+    long long vals[8] = {(long long)h->sub.size(), h->nif, h->if_iters, h->loc_ir, h->local_solves,
+                         h->slab_variant == 0 ? 0 : 1, h->if_krylov ? 1 : 0, h->tune_source};
+    for (int i = 0; i < nints && i < 8; ++i) ints[i] = (int)vals[i];
+    const double dv[3] = {h->if_res, h->tune_ms[0], h->tune_ms[1]};
+    for (int i = 0; dbl && i < ndbl && i < 3; ++i) dbl[i] = dv[i];
     return 0;
 }
 

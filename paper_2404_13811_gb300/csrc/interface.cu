@@ -1183,6 +1183,251 @@ __global__ void __launch_bounds__(GJ_THREADS) k_lu_inverse(IfPtrs I, const ElimD
     if (singular && tid == 0) atomicOr(status, ST_SINGULAR);
 }
 
+// ---------------------------------------------------------------------------
+// Slab inverse by blocked Gauss-Jordan elimination with partial pivoting
+// (FP32, in place) for slabs of at most GJI_T unknowns.  One cluster of CL
+// CTAs per slab; CTA r owns the panels q = r, r + CL, ... of GJI_NB columns in
+// shared memory.  For panel q its owner eliminates the panel's columns from
+// ALL rows (Gauss-Jordan), choosing each pivot among the rows not yet used as
+// pivots with the threshold rule of the slab LU (largest magnitude to 2^-12
+// relative, first row among equals); the panel then holds its transformed
+// columns P.  Every CTA applies the panel's row interchanges to its other
+// columns and adds (P - E_K) A[K, J], K the panel's pivot rows: a rank-NB
+// update.  After the last panel the storage holds (P_r A)^-1 for the
+// accumulated row permutation P_r, and column i goes to column rowperm[i] of
+// the inverse (A^-1 = (P_r A)^-1 P_r).  n^3 flops in one pass, against 2 n^3
+// for the LU factors followed by the inverse columns.
+// ---------------------------------------------------------------------------
+constexpr int GJI_T = 256;                 // threads per CTA: one panel row each
+constexpr int GJI_W = GJI_T / 32;
+constexpr int GJI_NB = 8;                  // panel width (the composite update of wider panels loses accuracy)
+
+size_t gji_smem(int np, int cl) {
+    const int npan = (np + GJI_NB - 1) / GJI_NB;
+    const int nq = (npan + cl - 1) / cl;   // panels owned by one CTA at most
+    return sizeof(float) * ((size_t)nq * GJI_NB * np + (size_t)GJI_NB * np + (size_t)GJI_NB * nq * GJI_NB +
+                            2 * GJI_W * GJI_NB) +
+           sizeof(int) * ((size_t)2 * np + 4 * GJI_NB + 2 * GJI_W) + 64;
+}
+
+__global__ void __launch_bounds__(GJI_T) k_gj_inverse(IfPtrs I, const ElimDev* el, int nel, int* status) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int CL = (int)cluster.num_blocks();
+    const int e = blockIdx.x / CL;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int np = I.npad;
+    const int npan = (np + GJI_NB - 1) / GJI_NB;
+    const int nqmax = (npan + CL - 1) / CL;
+    const int nq = rank < npan ? (npan - rank + CL - 1) / CL : 0;   // panels this CTA owns
+    const int ncol = nq * GJI_NB;                                  // owned column slots
+    extern __shared__ __align__(16) float gsm[];
+    float* Aown = gsm;                                       // [slot][np]: slot = local panel * NB + c
+    float* Pt = Aown + (size_t)nqmax * GJI_NB * np;          // [c][np]: P - E_K of the current panel
+    float* Tt = Pt + (size_t)GJI_NB * np;                    // [c][slot]: rows K of the owned columns
+    float* pub = Tt + (size_t)GJI_NB * nqmax * GJI_NB;       // [2][warp][NB] published candidate rows
+    int* rowperm = reinterpret_cast<int*>(pub + 2 * GJI_W * GJI_NB);   // [np] original row at each position
+    int* qpos = rowperm + np;                                // [np]
+    int* piv = qpos + np;                                    // [NB] the panel's pivot positions
+    int* aff = piv + GJI_NB;                                 // [2 NB] rows moved by the panel's interchanges
+    unsigned* pkey = reinterpret_cast<unsigned*>(aff + 2 * GJI_NB);    // [2][warp]
+    __shared__ int naff;
+    const bool active = e < nel;
+    const float* A = nullptr;
+    float* Ainv = nullptr;
+    if (active) {
+        const SlabDev S = I.slabs[el[e].j];
+        A = I.D + S.offD;
+        Ainv = I.Dinv + S.offD;
+        for (int s = warp; s < ncol; s += GJI_W) {
+            const int j = ((s / GJI_NB) * CL + rank) * GJI_NB + (s % GJI_NB);
+            for (int r = lane; r < np; r += 32) Aown[(size_t)s * np + r] = j < np ? __ldcg(&A[(size_t)j * np + r]) : 0.f;
+        }
+    }
+    for (int i = tid; i < np; i += nt) rowperm[i] = i;
+    bool singular = false;
+    __syncthreads();
+    for (int q = 0; q < npan; ++q) {
+        const int k0 = q * GJI_NB, b = min(GJI_NB, np - k0);
+        const int owner = q % CL, ql = q / CL;               // owner and its local panel index
+        const int par0 = 0;
+        (void)par0;
+        if (rank == owner && active) {
+            // ---- the panel: rows in registers (slot tid), logical positions lp ----
+            float x[GJI_NB];
+            const bool row = tid < np;
+            int lp = tid;
+            const float* pcol = Aown + (size_t)ql * GJI_NB * np;
+#pragma unroll
+            for (int c = 0; c < GJI_NB; ++c) x[c] = (row && c < b) ? pcol[(size_t)c * np + tid] : 0.f;
+#pragma unroll 1
+            for (int c = 0; c < b; ++c) {
+                const int r0 = k0 + c, par = c & 1;
+                float* pb = pub + par * GJI_W * GJI_NB;
+                unsigned key = 0u;
+                if (row && lp >= r0) {
+                    const float v = fabsf(x[0]);
+                    key = ((v == v ? __float_as_uint(v) : 0u) & ~0x7ffu) | (0x7ffu - (unsigned)(lp - r0));
+                }
+                const unsigned m = __reduce_max_sync(0xffffffffu, key);
+                if (key == m && m != 0u) {
+                    float4* dst = reinterpret_cast<float4*>(pb + warp * GJI_NB);
+#pragma unroll
+                    for (int q4 = 0; q4 < GJI_NB / 4; ++q4)
+                        dst[q4] = make_float4(x[4 * q4], x[4 * q4 + 1], x[4 * q4 + 2], x[4 * q4 + 3]);
+                }
+                if (lane == 0) pkey[par * GJI_W + warp] = m;
+                __syncthreads();
+                const unsigned km = lane < GJI_W ? pkey[par * GJI_W + lane] : 0u;
+                const unsigned bm = __reduce_max_sync(0xffffffffu, km);
+                const unsigned wb = __ballot_sync(0xffffffffu, km == bm && bm != 0u);
+                if (wb == 0u) {
+                    // no candidate (cannot happen while r0 < np): keep the order, flag it
+                    singular = true;
+                    if (tid == 0) piv[c] = r0;
+                    // column c: nothing to eliminate; the rotation below keeps the column order
+                } else {
+                    const int pw = __ffs(wb) - 1;
+                    const int p = r0 + 0x7ff - (int)(bm & 0x7ffu);
+                    if (tid == 0) piv[c] = p;
+                    const float4* src = reinterpret_cast<const float4*>(pb + pw * GJI_NB);
+                    float a = pb[pw * GJI_NB];
+                    if (a == 0.f) { singular = true; a = 1e-30f; }
+                    const float ip = __frcp_rn(a);
+                    if (lp == p) lp = r0;
+                    else if (lp == r0) lp = p;
+                    const bool isp = lp == r0;
+                    // pivot row: ip * row; other rows: row - (a_rc ip) * pivot row; column c takes ip / -a_rc ip
+                    const float f = x[0] * ip;
+                    const float g = isp ? -ip : f;
+                    const float c0 = isp ? ip : -f;
+#pragma unroll
+                    for (int q4 = 0; q4 < GJI_NB / 4; ++q4) {
+                        const float4 t = src[q4];
+                        if (q4 > 0) x[4 * q4] = (isp ? 0.f : x[4 * q4]) - g * t.x;
+                        x[4 * q4 + 1] = (isp ? 0.f : x[4 * q4 + 1]) - g * t.y;
+                        x[4 * q4 + 2] = (isp ? 0.f : x[4 * q4 + 2]) - g * t.z;
+                        x[4 * q4 + 3] = (isp ? 0.f : x[4 * q4 + 3]) - g * t.w;
+                    }
+                    x[0] = c0;
+                }
+                // rotate left with wrap-around: the next pivot column is x[0]
+                const float x0 = x[0];
+#pragma unroll
+                for (int cc = 0; cc < GJI_NB - 1; ++cc) x[cc] = x[cc + 1];
+                x[GJI_NB - 1] = x0;
+            }
+            // after b rotations register rr holds column (rr + b) mod NB; write the panel in
+            // logical row order, and P - E_K
+            if (row) {
+                float* dst = Aown + (size_t)ql * GJI_NB * np;
+#pragma unroll
+                for (int rr = 0; rr < GJI_NB; ++rr) {
+                    int c = rr + b;
+                    c = c >= GJI_NB ? c - GJI_NB : c;
+                    if (c < b) {
+                        dst[(size_t)c * np + lp] = x[rr];
+                        Pt[(size_t)c * np + lp] = x[rr] - (lp == k0 + c ? 1.f : 0.f);
+                    }
+                }
+            }
+        }
+        __threadfence();
+        cluster.sync();   // the panel (P - E_K) and its pivots are in the owner's shared memory
+        if (!active) continue;
+        if (rank != owner) {
+            const float* rP = cluster.map_shared_rank(Pt, owner);
+            const int* rpiv = cluster.map_shared_rank(piv, owner);
+            const float4* s4 = reinterpret_cast<const float4*>(rP);
+            float4* d4 = reinterpret_cast<float4*>(Pt);
+            for (int t = tid; t < (b * np) / 4; t += nt) d4[t] = s4[t];
+            for (int t = (b * np) / 4 * 4 + tid; t < b * np; t += nt) Pt[t] = rP[t];
+            if (tid < b) piv[tid] = rpiv[tid];
+        }
+        // the panel's interchanges composed into one permutation of at most 2 NB positions
+        for (int i = tid; i < np; i += nt) qpos[i] = i;
+        __syncthreads();
+        if (tid == 0) {
+            for (int c = 0; c < b; ++c) {
+                const int p = piv[c], t0 = qpos[k0 + c];
+                qpos[k0 + c] = qpos[p];
+                qpos[p] = t0;
+            }
+            naff = 0;
+        }
+        __syncthreads();
+        for (int i = tid; i < np; i += nt)
+            if (qpos[i] != i) aff[atomicAdd(&naff, 1)] = i;
+        __syncthreads();
+        const int na = naff;
+        {
+            const int rv = tid < na ? rowperm[qpos[aff[tid]]] : 0;
+            __syncthreads();
+            if (tid < na) rowperm[aff[tid]] = rv;
+        }
+        // owned columns other than this panel: interchanges, rows K saved, rank-NB update
+        for (int s = warp; s < ncol; s += GJI_W) {
+            if (rank == owner && s / GJI_NB == ql) continue;
+            float* col = Aown + (size_t)s * np;
+            float v0 = 0.f, v1 = 0.f;
+            if (lane < na) v0 = col[qpos[aff[lane]]];
+            if (lane + 32 < na) v1 = col[qpos[aff[lane + 32]]];
+            __syncwarp();
+            if (lane < na) col[aff[lane]] = v0;
+            if (lane + 32 < na) col[aff[lane + 32]] = v1;
+            __syncwarp();
+            if (lane < b) Tt[(size_t)lane * ncol + s] = col[k0 + lane];
+        }
+        __syncthreads();
+        {
+            // col[r] += sum_c Pt[c][r] T[c][s]: 4 x 4 register tiles (rows x slots)
+            const int ntr = (np + 3) / 4, nts = (ncol + 3) / 4;
+            for (int t = tid; t < ntr * nts; t += nt) {
+                const int ts = t / ntr, r = (t - ts * ntr) * 4, s0 = ts * 4;
+                bool skip[4];
+                float acc[4][4];
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int s = s0 + y;
+                    skip[y] = s >= ncol || (rank == owner && s / GJI_NB == ql);
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx) acc[xx][y] = 0.f;
+                }
+                for (int c = 0; c < b; ++c) {
+                    const float4 p4 = *reinterpret_cast<const float4*>(&Pt[(size_t)c * np + r]);
+                    float tv[4];
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) tv[y] = (s0 + y < ncol) ? Tt[(size_t)c * ncol + s0 + y] : 0.f;
+                    const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[xx][y] += pv[xx] * tv[y];
+                }
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    if (skip[y]) continue;
+                    float* col = Aown + (size_t)(s0 + y) * np;
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx)
+                        if (r + xx < np) col[r + xx] += acc[xx][y];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    // column i of the storage is column rowperm[i] of the inverse
+    for (int s = warp; s < ncol; s += GJI_W) {
+        const int i = ((s / GJI_NB) * CL + rank) * GJI_NB + (s % GJI_NB);
+        if (i >= np) continue;
+        float* dst = Ainv + (size_t)rowperm[i] * np;
+        for (int r = lane; r < np; r += 32) dst[r] = Aown[(size_t)s * np + r];
+    }
+    if (singular && tid == 0) atomicOr(status, ST_SINGULAR);
+}
+
 size_t lu_smem(int np, int xch) {
     const int npan = (np + GJ_NB - 1) / GJ_NB;
     const int ncmax = ((npan + LU_CL_MIN - 1) / LU_CL_MIN) * GJ_NB;   // the larger of the two cluster sizes' needs
@@ -1194,8 +1439,60 @@ size_t lu_smem(int np, int xch) {
 }
 
 
-cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
+// Gauss-Jordan slab inverses (k_gj_inverse) for slabs of at most GJI_T
+// unknowns: the largest cluster (8, 4, 2 CTAs) whose clusters for all the
+// launch's slabs fit on the GPU at once (occupancy query on the first launch
+// of a configuration, kept).
+static cudaError_t gj_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s) {
+    static int fits[3] = {-1, -1, -1};
+    static size_t fit_smem[3] = {0, 0, 0};
+    static size_t set_smem = 0;
+    const int cls[3] = {8, 4, 2};
+    int cl = 2;
+    for (int t = 0; t < 3; ++t) {
+        const size_t smem = gji_smem(I.npad, cls[t]);
+        if (smem > set_smem) {
+            cudaError_t e = cudaFuncSetAttribute(k_gj_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            set_smem = smem;
+        }
+        if (fits[t] < 0 || fit_smem[t] != smem) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cls[t]);
+            cfg.blockDim = dim3(GJI_T);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cls[t];
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_gj_inverse, &cfg) != cudaSuccess) {
+                (void)cudaGetLastError();
+                n = 0;
+            }
+            fits[t] = n;
+            fit_smem[t] = smem;
+        }
+        if (nel <= fits[t]) {
+            cl = cls[t];
+            break;
+        }
+    }
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&el, &nel, &status};
+    return launch_cluster((const void*)k_gj_inverse, nel * cl, GJI_T, gji_smem(I.npad, cl), s, args, cl);
+}
+
+// Slab inverses of one elimination level.  variant 0: Gauss-Jordan where
+// the slabs are small enough (else the LU); 1: the LU with inverse columns.
+int slab_inverse_gj_ok(int npad) { return npad <= GJI_T; }
+
+cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, int variant, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
+    if (variant == 0 && I.npad <= GJI_T) return gj_inverse(I, el, nel, status, s);
     const size_t smem = lu_smem(I.npad, I.xch);
     // panel rows per thread: one for slabs of up to GJ_THREADS unknowns, else two
     const bool two = I.npad > GJ_THREADS;

@@ -45,6 +45,8 @@ extern "C" {
 #define MRCM_ERR_SINGULAR (-6)       /* zero pivot in the interface factorisation */
 #define MRCM_ERR_UNSUPPORTED (-7)    /* a size or option this build does not handle */
 #define MRCM_ERR_NOMEM (-8)          /* device allocation failed */
+#define MRCM_ERR_TIMEOUT (-9)        /* a kernel's bounded wait (for a staged copy) ran out; the kernel
+                                        returned without its result (the context stays usable) */
 
 #define MRCM_NEUMANN 0   /* u.n = value on the side (Eq. (1d)) */
 #define MRCM_DIRICHLET 1 /* p = value on the side (Eq. (1c)) */
@@ -90,9 +92,9 @@ typedef struct {
  *   alpha_smooth the same for the smoothing solves (Sec. 3 uses 1).
  *   precision    MRCM_FP64 or MRCM_MIXED.
  *   ir_tol       relative residual (inf-norm; Jacobi-scaled for the local
- *                solves) that refinement must reach (mixed local solves and
- *                the interface solve; the FP64 form refines its interface
- *                solve on to 1e-2 ir_tol).  3D local solves refine on to their
+ *                solves, row-equilibrated for the interface solve) that
+ *                refinement must reach (mixed local solves and
+ *                the interface solve).  3D local solves refine on to their
  *                residual floor: they stop at 1e-3 ir_tol, or below ir_tol
  *                once the residual no longer halves per step.
  *   max_ir       maximum refinement steps. */

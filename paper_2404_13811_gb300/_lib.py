@@ -19,7 +19,7 @@ MRCM_FP64, MRCM_MIXED = 0, 1
 ERRORS = {
     -1: "MRCM_ERR_BAD_INPUT", -2: "MRCM_ERR_STATE", -3: "MRCM_ERR_CUDA", -4: "MRCM_ERR_NOT_SPD",
     -5: "MRCM_ERR_NO_CONVERGENCE", -6: "MRCM_ERR_SINGULAR", -7: "MRCM_ERR_UNSUPPORTED",
-    -8: "MRCM_ERR_NOMEM",
+    -8: "MRCM_ERR_NOMEM", -9: "MRCM_ERR_TIMEOUT",
 }
 
 

@@ -440,6 +440,14 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     h->mth.ir_tol = h->prm.ir_tol > 0 ? h->prm.ir_tol : 1e-12;
     h->mth.max_ir = prec == MRCM_FP64 ? 1 : h->prm.max_ir;
     h->mth.same_alpha = h->prm.alpha_basis == h->prm.alpha_smooth;
+    // The smoothing kernel waits up to 2^31 cycles for its staged copy.  For
+    // the failure-detection test only, MRCM_TEST_FIRST_WAIT_CYCLES = N > 0
+    // makes its first wait one of N cycles for a barrier nothing arrives at:
+    // it runs out, the kernel waits again at the full limit for the copy in
+    // flight, skips its solve and flags it (MRCM_ERR_TIMEOUT).
+    h->mth.wait0 = 0;
+    if (const char* w = std::getenv("MRCM_TEST_FIRST_WAIT_CYCLES"))
+        if (*w) h->mth.wait0 = std::max(0LL, std::atoll(w));
 
     // jobs: basis, particular, smoothing factor
     std::map<int, std::vector<Job>> byw;
@@ -711,7 +719,7 @@ static int check_status(mrcm_handle* h) {
     h->loc_ir = std::max(h->loc_ir, st[1]);
     if (st[0] & ST_NOT_SPD) return fail(h, MRCM_ERR_NOT_SPD, "non-positive pivot in a local factorisation (item " + std::to_string(st[2]) + ")");
     if (st[0] & ST_NO_CONV) return fail(h, MRCM_ERR_NO_CONVERGENCE, "local iterative refinement did not reach ir_tol");
-    if (st[0] & ST_BAD) return fail(h, MRCM_ERR_CUDA, "a staged copy did not complete in time");
+    if (st[0] & ST_BAD) return fail(h, MRCM_ERR_TIMEOUT, "a staged copy did not complete within its wait limit");
     return 0;
 }
 
@@ -997,6 +1005,9 @@ int mrcm_build_basis(mrcm_handle* h) {
     return 0;
 }
 
+// The interface refinement's target (relative, row-equilibrated max norm).
+static double if_target(const mrcm_handle* h) { return h->mth.ir_tol; }
+
 // Interface fallback when the refinement stalls: restarted GMRES in FP64 on
 // G X = rhs, right-preconditioned by the FP32 reduction (the row scaling, the
 // sweeps and the column scaling of one refinement step), started from the
@@ -1037,7 +1048,7 @@ static int krylov_interface(mrcm_handle* h, double* worst_out) {
     };
     if (int e = dot(h->I.rhs, h->I.rhs, &rhs2)) return e;
     // the inner test, on the 2-norm, with a margin for the max-norm test that ends a cycle
-    const double target = 1e-2 * h->mth.ir_tol * std::sqrt(rhs2);
+    const double target = 1e-2 * if_target(h) * std::sqrt(rhs2);
     IfPtrs J = h->I;   // G v: x = v, rhs = 0, result (-G v) into w
     J.rhs = zero;
     J.r = w;
@@ -1047,7 +1058,7 @@ static int krylov_interface(mrcm_handle* h, double* worst_out) {
         if (int e = issue_residual(h)) return e;
         if (int e = read_if_residual(h, &worst)) return e;
         if (!std::isfinite(worst)) return fail(h, MRCM_ERR_SINGULAR, "interface Krylov iteration diverged");
-        if (worst <= h->mth.ir_tol) break;
+        if (worst <= if_target(h)) break;
         double beta2 = 0.0;
         if (int e = dot(h->I.r, h->I.r, &beta2)) return e;
         const double beta = std::sqrt(beta2);
@@ -1165,13 +1176,6 @@ struct RefineOut {
 // limit, or when a step no longer reduces the residual below 0.9 of the
 // previous one: then the FP32 factors are too poor a preconditioner for
 // stationary refinement of this system).
-// The interface refinement's target: ir_tol, in the FP64 form 1e-2 ir_tol
-// (that form is the full-FP64 reference of the method, so its interface
-// solve goes on towards the FP64 residual floor).
-static double if_target(const mrcm_handle* h) {
-    return h->prm.precision == MRCM_FP64 ? 1e-2 * h->mth.ir_tol : h->mth.ir_tol;
-}
-
 static int factor_refine(mrcm_handle* h, RefineOut* o, std::string* hist) {
     DevTimer tm(h);
     tm.start();

@@ -11,8 +11,19 @@ namespace {
 
 constexpr int NWARP = 4;
 
-// 1/x in FP64: FP32 reciprocal refined by two Newton steps (error ~ u_64).
+// FP32 normal range of an FP64 value, from its exponent bits (integer pipe).
+__device__ __forceinline__ bool in_f32_range(double x) {
+    const unsigned e11 = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    return e11 >= 1023u - 126u && e11 <= 1023u + 126u;   // 2^-126 <= |x| < 2^127
+}
+
+// 1/x in FP64 by Newton-Raphson iteration for the reciprocal, r <- r (2 - x r),
+// from the correctly rounded FP32 reciprocal of x: each step squares the
+// relative error (about 2^-23 for the seed, below the FP64 rounding after two
+// steps), without the FP64 division.  Outside the FP32 normal range the seed
+// would be 0 or infinite, and the FP64 division is used.
 __device__ __forceinline__ double rcp64(double x) {
+    if (!in_f32_range(x)) return 1.0 / x;
     double r = (double)__frcp_rn((float)x);
     r = r * (2.0 - x * r);
     r = r * (2.0 - x * r);
@@ -292,8 +303,10 @@ __device__ __forceinline__ void form_line(T (&a)[BW], const Ops& O, const T* cys
         if (up) d = fma(-cu2, f2d_bits(up[ii * ld + ii]), d);
         if (dn) d = fma(-cn2, f2d_bits(dn[ii * ld + ii]), d);
     } else {
-        if (up) d -= (double)cu * (double)cu * (double)up[ii * ld + ii];
-        if (dn) d -= (double)cn * (double)cn * (double)dn[ii * ld + ii];
+        // c (c S_ii), not c^2 S_ii: c^2 leaves the FP64 range for couplings
+        // below ~1e-154 (permeabilities scaled that far), c S_ii does not
+        if (up) d -= (double)cu * ((double)cu * (double)up[ii * ld + ii]);
+        if (dn) d -= (double)cn * ((double)cn * (double)dn[ii * ld + ii]);
     }
     T dT;
     if constexpr (VEC) dT = d2f_bits(d);
@@ -1156,7 +1169,7 @@ __device__ void setup_box(Box& B, const MemberDev& md, const int* lo, const int*
 
 __device__ void fill_scale(const Box& B, Ops& O, bool mixed) {
     for (int c = threadIdx.x; c < B.n; c += blockDim.x)
-        O.dsc[c] = mixed ? (double)rsqrtf((float)O.cd[c]) : 1.0;
+        O.dsc[c] = !mixed ? 1.0 : in_f32_range(O.cd[c]) ? (double)rsqrtf((float)O.cd[c]) : 1.0 / sqrt(O.cd[c]);
     __syncthreads();
 }
 
@@ -1179,9 +1192,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Waits for phase `parity` of the barrier for at most ~2^31 cycles (about a
-// second); false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for phase `parity` of the barrier for at most `limit` cycles (2^31,
+// about a second, by default); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 1LL << 31) {
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
@@ -1191,7 +1204,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 

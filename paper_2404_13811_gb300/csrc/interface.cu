@@ -380,10 +380,13 @@ __global__ void k_if_residual(IfPtrs I, const int* row_member, int nrows, int fi
         for (int k = 0; k < nc; ++k) s -= gv[b * I.NB + k] * I.x[c0 + k];
     }
     I.r[row] = s;
-    I.bq[row] = (float)(I.R[row] * s);
+    const double rs = I.R[row] * s;
+    I.bq[row] = (float)rs;
+    // norms of the row-equilibrated residual and right-hand side: each row on
+    // its own scale (the flux rows scale with K, the pressure rows do not)
     const int m = row_member[row];
-    atomic_max_pos(&I.rnorm[2 * m], fabs(s));
-    if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(I.rhs[row]));
+    atomic_max_pos(&I.rnorm[2 * m], fabs(rs));
+    if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(I.R[row] * I.rhs[row]));
 }
 
 // Warp-cooperative dot product of a row-major matrix row with a shared vector.
@@ -581,10 +584,11 @@ __global__ void k_if_residualT(IfPtrs I, const SubDev* sub, const int* col_item,
         }
     }
     I.r[c] = s;
-    I.bq[c] = (float)(I.Cs[c] * s);
+    const double cs = I.Cs[c] * s;
+    I.bq[c] = (float)cs;
     const int m = row_member[c];
-    atomic_max_pos(&I.rnorm[2 * m], fabs(s));
-    if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(z[c]));
+    atomic_max_pos(&I.rnorm[2 * m], fabs(cs));
+    if (first) atomic_max_pos(&I.rnorm[2 * m + 1], fabs(I.Cs[c] * z[c]));
 }
 
 // B_l^T for the eliminations of one level: v_jm -= Cdn_j^T (Dinv_j[:, vrows]^T v_j)

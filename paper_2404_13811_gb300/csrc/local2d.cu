@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     const MemberDev& md = P.mem[sd.member];
     __shared__ Box B;
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t never;   // failure-detection test only: a barrier nothing arrives at
     if (threadIdx.x == 0) setup_box(B, md, sd.loh, sd.hih, Mth.alpha_s);
     __syncthreads();
     const size_t n = (size_t)B.n;
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         flags[0] = 0;
         flags[1] = 0;
         mbar_init(&bar, 1);
+        if (Mth.wait0 > 0) mbar_init(&never, 1);
         mbar_expect_tx(&bar, pbytes);
         bulk_g2s(smem, Pg, pbytes, &bar);
     }
@@ -320,7 +322,9 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     }
     int it = 0;
     // every thread reads the staged pack: all wait for the copy, and agree on a late one
-    const bool arrived = mbar_wait(&bar, 0);
+    // (with the failure-detection test's wait set, the first wait is for a
+    // barrier nothing arrives at, for that many cycles: it runs out)
+    const bool arrived = Mth.wait0 > 0 ? mbar_wait(&never, 0, Mth.wait0) : mbar_wait(&bar, 0);
     if (!__syncthreads_or(!arrived)) {
         for (int sid = 0; sid < 4; ++sid) {
             if (B.kind[sid] != 2) continue;

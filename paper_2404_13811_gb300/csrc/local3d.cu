@@ -178,7 +178,7 @@ __device__ void build_ops3(const Box3& B, const MemberDev& md, const DevPtrs& P,
             }
         }
         O.cd[t] = d;
-        if (mixed) O.dsc[t] = (double)rsqrtf((float)d);
+        if (mixed) O.dsc[t] = in_f32_range(d) ? (double)rsqrtf((float)d) : 1.0 / sqrt(d);
     }
     __syncthreads();
 }
@@ -299,7 +299,7 @@ __device__ void factor3(const Box3& B, const Ops3& O, const T* c2s, T* F, T* Sb,
                 double s = O.cd[ci] * si * si;
                 if (j > 0) {
                     const double cc = (double)c2s[ci - b];
-                    s -= cc * cc * (double)Sb[sidx];
+                    s -= cc * (cc * (double)Sb[sidx]);   // not cc^2 (range at tiny couplings)
                 }
                 Sb[sidx] = (T)s;
             } else {

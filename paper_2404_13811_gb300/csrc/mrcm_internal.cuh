@@ -102,6 +102,7 @@ struct MethodDev {
     double ir_tol;
     int max_ir;
     int same_alpha;
+    long long wait0;   // cycle limit of the first wait for a staged copy in the 2D smoothing kernel
 };
 
 
@@ -154,7 +155,7 @@ struct AdjPtrs {
 #define ST_NOT_SPD 1
 #define ST_NO_CONV 2
 #define ST_SINGULAR 4
-#define ST_BAD 8
+#define ST_BAD 8         // a staged (bulk) copy did not arrive within its wait limit
 #define ST_BAD_K 16      // a permeability that is not positive and finite
 
 static inline __host__ __device__ int side_axis(int sid) { return sid >> 1; }

@@ -4,7 +4,6 @@
 #include "mrcm_internal.cuh"
 #include <algorithm>
 
-__device__ __forceinline__ double harm_t(double a, double b) { return 2.0 * a * b / (a + b); }
 
 // One CTA per subdomain: p = pbar + sum_k X_k Psi_k on Omega_i, Gamma_i
 // velocities ubar + sum_k X_k U_k, interior faces from the assembled
@@ -49,7 +48,8 @@ __global__ void k_assemble2d(DevPtrs P, const double* __restrict__ X) {
             if (!edge) {
                 const int cn = c + (a == 0 ? (hi ? 1 : -1) : (hi ? nIx : -nIx));
                 const long long gn = g + (a == 0 ? (hi ? 1 : -1) : (hi ? md.n[0] : -md.n[0]));
-                const double T = area * 2.0 * kc * K[gn] / (h * (kc + K[gn]));
+                const double kn = K[gn];
+                const double T = area * 2.0 * kc * (kn / (kc + kn)) / h;   // no K_L K_R product (range)
                 uo = T * (pc - ps[cn]) / area;
             } else if (sd.side_mask & (1 << sid)) {
                 const int e = a == 0 ? j : i;
@@ -132,8 +132,10 @@ __global__ void k_faces(const MemberDev* mem, int nmem, const double* K, double*
             hh = md.h[a] / (2.0 * kc);
             if (idx[a] < md.n[a] - 1) {
                 const double kn = K[g + st[a]];
-                T = area * 2.0 * kc * kn / (md.h[a] * (kc + kn));
-                w = md.Hw[a] * (kc + kn) / (2.0 * kc * kn);
+                // harmonic-mean laws written without the product K_L K_R, which
+                // leaves the FP64 range for permeabilities beyond ~1e+-154
+                T = area * 2.0 * kc * (kn / (kc + kn)) / md.h[a];
+                w = md.Hw[a] * 0.5 * (1.0 / kc + 1.0 / kn);
             }
         }
         Tf[g * 3 + a] = T;

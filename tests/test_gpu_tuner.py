@@ -1,0 +1,42 @@
+"""The slab-inverse autotuner of the interface solve: a handle measures both
+variants on its first solve, writes its choice to the cache named by
+MRCM_TUNE_CACHE, and a second handle of the same shape class takes the choice
+from the cache and reproduces the first handle's solution bit for bit."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2404_13811_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(case):
+    from paper_2404_13811_gb300 import _lib as L
+    from paper_2404_13811_gb300.solver import MRCM
+    pm = case.params
+    s = MRCM(case.problem, case.partition, space=pm.space, alpha_basis=pm.alpha_basis,
+             alpha_smooth=pm.alpha_smooth, precision="mixed")
+    s.run(1)
+    st = L.mrcm_stats(s.h)
+    p, u = s.fluxes()
+    s.close()
+    return st, p, u
+
+
+def test_tuning_cache_round_trip(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("MRCM_TUNE_CACHE", str(cache))
+    case = I.config_channel2d(n=128, n_smooth=1)
+    st1, p1, u1 = _run(case)
+    assert st1["slab_inverse_source"] == "measured", st1
+    assert st1["tune_ms"]["gauss-jordan"] > 0 and st1["tune_ms"]["lu"] > 0, st1
+    entries = json.loads(cache.read_text())
+    assert len(entries) == 1
+    (key, entry), = entries.items()
+    assert key.startswith("interface dim2 ") and entry["slab_inverse"] == st1["slab_inverse"], (key, entry)
+    assert entry["gauss_jordan_steps"] > 0 and entry["lu_steps"] > 0
+    st2, p2, u2 = _run(case)
+    assert st2["slab_inverse_source"] == "cache" and st2["slab_inverse"] == st1["slab_inverse"], st2
+    assert np.array_equal(p1, p2) and np.array_equal(u1, u2)

@@ -241,24 +241,28 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
  * ints[1] = interface unknowns, ints[2] = interface refinement steps of the
  * last solve, ints[3] = largest local refinement count of the last
  * build/smooth call, ints[4] = local solves performed so far, ints[5] = the
- * slab inverses of the interface reduction (0 Gauss-Jordan, 1 LU: chosen per
- * handle by the autotuner below), ints[6] = 1 when the last interface solve
- * needed the GMRES fallback, ints[7] = where the slab-inverse choice came from
- * (0 not made or not a choice: slabs larger than 256 unknowns always use the
- * LU; 1 the tuning cache; 2 measured on this handle's first interface solve);
- * dbl[0] = last interface relative residual, dbl[1] / dbl[2] = the measured
- * device ms of the Gauss-Jordan / LU variant (factorisation + refinement to
- * ir_tol; 0 when not measured).  Either pointer may be NULL; at most nints /
- * ndbl entries are written.
+ * slab inverses of the interface reduction (0 blocked Gauss-Jordan, 1 LU, 2
+ * register-resident Gauss-Jordan: chosen per handle by the autotuner below),
+ * ints[6] = 1 when the last interface solve needed the GMRES fallback,
+ * ints[7] = where the slab-inverse choice came from (0 not made or not a
+ * choice: slabs larger than 512 unknowns always use the LU; 1 the tuning
+ * cache; 2 measured on this handle's first interface solve); dbl[0] = last
+ * interface relative residual, dbl[1] / dbl[2] / dbl[3] = the measured device
+ * ms of variants 0 / 1 / 2 (factorisation + refinement to ir_tol; 0 when not
+ * measured).  Either pointer may be NULL; at most nints / ndbl entries are
+ * written.
  *
  * Autotuner.  The slab inverses of the interface reduction are computed by
- * blocked Gauss-Jordan elimination (one pass, for slabs of at most 256
- * unknowns) or by an LU factorisation followed by the inverse columns.  The
- * first mrcm_solve_interface of a handle (and the first after
- * mrcm_set_permeability) times both -- device time of the factorisation and
- * of the refinement steps it needs -- and keeps the faster one that reaches
- * ir_tol; a later refinement that stalls with Gauss-Jordan switches the handle
- * to the LU.  With the environment variable MRCM_TUNE_CACHE naming a JSON file,
+ * one of: Gauss-Jordan elimination with the slab held in registers across a
+ * cluster of CTAs (one pivot column per step, slabs of at most 512
+ * unknowns); blocked Gauss-Jordan elimination in shared memory (slabs of at
+ * most 256 unknowns); an LU factorisation followed by the inverse columns
+ * (any size).  The first mrcm_solve_interface of a handle (and the first
+ * after mrcm_set_permeability) times every admissible variant -- device time
+ * of the factorisation and of the refinement steps it needs -- and keeps the
+ * fastest one that reaches ir_tol (the LU when none does); a later
+ * refinement that stalls with a Gauss-Jordan variant switches the handle to
+ * the LU.  With the environment variable MRCM_TUNE_CACHE naming a JSON file,
  * the choice is read from it by shape class (dimension, slab size, slab and
  * level counts, members, precision, space, ir_tol) when present and written to
  * it after a measurement. */
@@ -282,6 +286,15 @@ int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl
  * is enabled. */
 int mrcm_profile(mrcm_handle* h, int enable);
 int mrcm_timings(mrcm_handle* h, double* ms, long long* launches, int n);
+
+/* Measurement support (the paper has no counterpart): the sustained FMA
+ * throughput of the current device in FP32 and in FP64, in TFLOP/s (2 flops
+ * per FMA), from independent FMA chains on every SM timed with CUDA events
+ * on cuda_stream (the median of three runs; about a second of device time in
+ * all).  Used as the denominators of the FP32 / FP64 rooflines.  Allocates a
+ * small device buffer while it runs; changes no device setting.  Either
+ * pointer may be NULL (that measurement is skipped).  Synchronises. */
+int mrcm_measure_fma_peaks(double* fp32_tflops, double* fp64_tflops, void* cuda_stream);
 
 int mrcm_destroy(mrcm_handle* h);
 

@@ -42,7 +42,9 @@ class mrcm_params(C.Structure):
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
            "mrcm_smooth", "mrcm_run", "mrcm_fluxes", "mrcm_fluxes_static", "mrcm_set_permeability",
-           "mrcm_adjoint", "mrcm_backward", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_destroy", "mrcm_last_error"]
+           "mrcm_adjoint", "mrcm_backward", "mrcm_stats", "mrcm_profile", "mrcm_timings", "mrcm_measure_fma_peaks",
+           "mrcm_destroy", "mrcm_last_error"]
+SLAB_INVERSES = {0: "gauss-jordan", 1: "lu", 2: "gauss-jordan-registers"}
 PHASES = ["local_basis", "interface_factor", "interface_refine", "assemble", "smooth", "graph", "interface_lu"]
 
 _lib = None
@@ -232,13 +234,14 @@ def mrcm_backward(h, dL_du, dL_dp, dL_dlogK):
 def mrcm_stats(h):
     lib = load()
     ints = (C.c_int * 8)()
-    dbl = (C.c_double * 3)()
-    _check(lib, h, lib.mrcm_stats(h, ints, 8, dbl, 3))
+    dbl = (C.c_double * 4)()
+    _check(lib, h, lib.mrcm_stats(h, ints, 8, dbl, 4))
     return {"subdomains": ints[0], "interface_unknowns": ints[1], "interface_ir_steps": ints[2],
             "local_ir_steps": ints[3], "local_solves": ints[4],
-            "slab_inverse": "gauss-jordan" if ints[5] == 0 else "lu", "interface_gmres": bool(ints[6]),
+            "slab_inverse": SLAB_INVERSES.get(ints[5], ints[5]), "interface_gmres": bool(ints[6]),
             "slab_inverse_source": {0: "fixed", 1: "cache", 2: "measured"}.get(ints[7], ints[7]),
-            "interface_residual": dbl[0], "tune_ms": {"gauss-jordan": dbl[1], "lu": dbl[2]}}
+            "interface_residual": dbl[0],
+            "tune_ms": {"gauss-jordan": dbl[1], "lu": dbl[2], "gauss-jordan-registers": dbl[3]}}
 
 
 def mrcm_profile(h, enable):
@@ -263,3 +266,13 @@ def mrcm_destroy(h):
 
 def mrcm_last_error(h):
     return load().mrcm_last_error(h).decode()
+
+
+def mrcm_measure_fma_peaks(stream=0):
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    lib = load()
+    lib.mrcm_measure_fma_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]
+    a, b = C.c_double(), C.c_double()
+    rc = lib.mrcm_measure_fma_peaks(C.byref(a), C.byref(b), C.c_void_p(int(stream)))
+    _check(lib, None, rc)
+    return a.value, b.value

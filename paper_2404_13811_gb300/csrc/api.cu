@@ -50,6 +50,7 @@ cudaError_t kry_dot(const double* a, const double* b, int n, double* part, cudaS
 int kry_blocks();
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, int variant, cudaStream_t s);
 int slab_inverse_gj_ok(int npad);
+int slab_inverse_gjr_npad(int npad);
 size_t elim_smem_bytes(int nmv, int cw);
 size_t lu_smem(int np, int xch);
 size_t local3d_smem(int prec, int nx, int ny, int nz, bool part);
@@ -175,9 +176,10 @@ struct mrcm_handle {
     int if_iters = 0;
     double if_res = 0.0;
     bool if_krylov = false;       // the last interface solve needed the GMRES fallback
-    int slab_variant = -1;        // slab inverses: -1 not chosen yet, 0 Gauss-Jordan, 1 LU (autotuner)
+    int slab_variant = -1;        // slab inverses: -1 not chosen yet, 0 blocked Gauss-Jordan, 1 LU,
+                                  // 2 register-resident Gauss-Jordan (autotuner)
     int tune_source = 0;          // 0 none, 1 from the tuning cache, 2 measured by this handle
-    double tune_ms[2] = {0.0, 0.0};   // measured device ms (factor + refine) of Gauss-Jordan / LU
+    double tune_ms[3] = {0.0, 0.0, 0.0};   // measured device ms (factor + refine) of each variant
     double* d_kry = nullptr;      // its workspace (allocated on first use)
     int loc_ir = 0;
     long long local_solves = 0;
@@ -1217,8 +1219,10 @@ static int factor_refine(mrcm_handle* h, RefineOut* o, std::string* hist) {
 
 // The autotuner's cache (environment MRCM_TUNE_CACHE = a JSON file): one
 // object per shape class of the interface reduction, keyed by tune_key,
-// holding the chosen slab inverses and the measured device times of both
-// variants (factorisation + refinement to ir_tol).
+// holding the chosen slab inverses and the measured device times of the
+// variants tried (factorisation + refinement to ir_tol; 0 when not tried).
+static const char* const kSlabNames[3] = {"gauss-jordan", "lu", "gauss-jordan-registers"};
+
 static std::string tune_key(const mrcm_handle* h) {
     char buf[192];
     snprintf(buf, sizeof(buf), "interface dim%d npad%d slabs%zu levels%zu members%zu prec%d space%d tol%.0e", h->dim,
@@ -1239,13 +1243,17 @@ static int tune_cache_lookup(const std::string& key) {
         const char* q = std::strstr(line, tag.c_str());
         if (!q) continue;
         q += tag.size();
-        v = std::strncmp(q, "lu", 2) == 0 ? 1 : std::strncmp(q, "gauss-jordan", 12) == 0 ? 0 : -1;
+        v = -1;
+        for (int c = 0; c < 3; ++c) {
+            const size_t len = std::strlen(kSlabNames[c]);
+            if (std::strncmp(q, kSlabNames[c], len) == 0 && q[len] == '"') v = c;
+        }
     }
     std::fclose(f);
     return v;
 }
 
-static void tune_cache_store(const std::string& key, int variant, double ms_gj, double ms_lu, int it_gj, int it_lu) {
+static void tune_cache_store(const std::string& key, int variant, const double* ms, const int* steps) {
     const char* path = std::getenv("MRCM_TUNE_CACHE");
     if (!path || !*path) return;
     std::vector<std::string> keep;
@@ -1263,8 +1271,8 @@ static void tune_cache_store(const std::string& key, int variant, double ms_gj, 
     char buf[512];
     snprintf(buf, sizeof(buf),
              "  \"%s\": {\"slab_inverse\": \"%s\", \"gauss_jordan_ms\": %.4f, \"gauss_jordan_steps\": %d, "
-             "\"lu_ms\": %.4f, \"lu_steps\": %d}",
-             key.c_str(), variant == 0 ? "gauss-jordan" : "lu", ms_gj, it_gj, ms_lu, it_lu);
+             "\"lu_ms\": %.4f, \"lu_steps\": %d, \"gauss_jordan_registers_ms\": %.4f, \"gauss_jordan_registers_steps\": %d}",
+             key.c_str(), kSlabNames[variant], ms[0], steps[0], ms[1], steps[1], ms[2], steps[2]);
     keep.push_back(buf);
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = std::fopen(tmp.c_str(), "w");
@@ -1283,39 +1291,49 @@ int mrcm_solve_interface(mrcm_handle* h) {
     std::string hist;
     RefineOut o;
     int rc = 0;
-    const bool gj_ok = slab_inverse_gj_ok(h->npad);
-    if (!gj_ok) h->slab_variant = 1;
+    // the slab inverses this interface system admits: register-resident
+    // Gauss-Jordan (slabs of up to 512 unknowns), blocked Gauss-Jordan (up to
+    // 256), and the LU (any size)
+    std::vector<int> cands;
+    if (slab_inverse_gjr_npad(h->npad)) cands.push_back(2);
+    if (slab_inverse_gj_ok(h->npad)) cands.push_back(0);
+    cands.push_back(1);
+    if (h->slab_variant >= 0 && std::find(cands.begin(), cands.end(), h->slab_variant) == cands.end())
+        h->slab_variant = 1;
+    if (h->slab_variant < 0 && cands.size() == 1) h->slab_variant = 1;
     if (h->slab_variant < 0) {
-        // autotuner: the cached choice for this shape class, else both slab
-        // inverses timed on this solve (device time of the factorisation and
-        // the refinement steps) and the faster one that converges kept
+        // autotuner: the cached choice for this shape class, else every
+        // admissible slab inverse timed on this solve (device time of the
+        // factorisation and the refinement steps) and the fastest one that
+        // converges kept (the LU when none does)
         const std::string key = tune_key(h);
         const int cached = tune_cache_lookup(key);
-        if (cached >= 0) {
+        if (cached >= 0 && std::find(cands.begin(), cands.end(), cached) != cands.end()) {
             h->slab_variant = cached;
             h->tune_source = 1;
         } else {
-            RefineOut a, b;
-            h->slab_variant = 0;
-            hist += " [gauss-jordan]";
-            if ((rc = factor_refine(h, &a, &hist))) return rc;
-            const bool a_ok = a.worst <= if_target(h);
-            h->slab_variant = 1;
-            hist += " [lu]";
-            if ((rc = factor_refine(h, &b, &hist))) return rc;
-            const bool b_ok = b.worst <= if_target(h);
-            const int choice = (a_ok && (!b_ok || a.ms < b.ms)) ? 0 : 1;
-            h->tune_ms[0] = a.ms;
-            h->tune_ms[1] = b.ms;
+            RefineOut run[3];
+            bool ok[3] = {false, false, false};
+            int steps[3] = {0, 0, 0};
+            for (int c : cands) {
+                h->slab_variant = c;
+                hist += std::string(" [") + kSlabNames[c] + "]";
+                if ((rc = factor_refine(h, &run[c], &hist))) return rc;
+                ok[c] = run[c].worst <= if_target(h);
+                h->tune_ms[c] = run[c].ms;
+                steps[c] = run[c].it;
+            }
+            int choice = 1;
+            for (int c : cands)
+                if (ok[c] && (!ok[choice] || run[c].ms < run[choice].ms)) choice = c;
             h->tune_source = 2;
-            tune_cache_store(key, choice, a.ms, b.ms, a.it, b.it);
+            tune_cache_store(key, choice, h->tune_ms, steps);
             h->slab_variant = choice;
-            if (choice == 0) {
-                // the handle's state is the LU run's: solve again with the choice
-                hist += " [gauss-jordan]";
-                if ((rc = factor_refine(h, &o, &hist))) return rc;
+            if (choice == cands.back()) {
+                o = run[choice];   // the handle's state is the last run's
             } else {
-                o = b;
+                hist += std::string(" [") + kSlabNames[choice] + "]";
+                if ((rc = factor_refine(h, &o, &hist))) return rc;
             }
         }
     }
@@ -1324,7 +1342,7 @@ int mrcm_solve_interface(mrcm_handle* h) {
     }
     h->if_krylov = false;
     const int max_it = std::max(8, h->prm.max_ir);
-    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it) && h->slab_variant == 0) {
+    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it) && h->slab_variant != 1) {
         // the Gauss-Jordan slab inverses are the less accurate preconditioner on
         // very ill-conditioned interface systems: refactor with the slab LU and
         // refine again (the handle keeps the LU for its later solves and captures)
@@ -1613,10 +1631,10 @@ int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_l
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     long long vals[8] = {(long long)h->sub.size(), h->nif, h->if_iters, h->loc_ir, h->local_solves,
-                         h->slab_variant == 0 ? 0 : 1, h->if_krylov ? 1 : 0, h->tune_source};
+                         h->slab_variant < 0 ? 1 : h->slab_variant, h->if_krylov ? 1 : 0, h->tune_source};
     for (int i = 0; i < nints && i < 8; ++i) ints[i] = (int)vals[i];
-    const double dv[3] = {h->if_res, h->tune_ms[0], h->tune_ms[1]};
-    for (int i = 0; dbl && i < ndbl && i < 3; ++i) dbl[i] = dv[i];
+    const double dv[4] = {h->if_res, h->tune_ms[0], h->tune_ms[1], h->tune_ms[2]};
+    for (int i = 0; dbl && i < ndbl && i < 4; ++i) dbl[i] = dv[i];
     return 0;
 }
 

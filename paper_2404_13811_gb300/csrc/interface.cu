@@ -1490,12 +1490,17 @@ static cudaError_t gj_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* 
     return launch_cluster((const void*)k_gj_inverse, nel * cl, GJI_T, gji_smem(I.npad, cl), s, args, cl);
 }
 
-// Slab inverses of one elimination level.  variant 0: Gauss-Jordan where
-// the slabs are small enough (else the LU); 1: the LU with inverse columns.
+// Slab inverses of one elimination level.  variant 0: blocked Gauss-Jordan
+// where the slabs are small enough (else the LU); 1: the LU with inverse
+// columns; 2: register-resident Gauss-Jordan (slab_gjr.cu) where the slabs
+// are small enough (else the LU).
 int slab_inverse_gj_ok(int npad) { return npad <= GJI_T; }
+int slab_inverse_gjr_npad(int npad);
+cudaError_t gjr_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, cudaStream_t s);
 
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, int variant, cudaStream_t s) {
     if (nel == 0) return cudaSuccess;
+    if (variant == 2 && slab_inverse_gjr_npad(I.npad)) return gjr_inverse(I, el, nel, status, s);
     if (variant == 0 && I.npad <= GJI_T) return gj_inverse(I, el, nel, status, s);
     const size_t smem = lu_smem(I.npad, I.xch);
     // panel rows per thread: one for slabs of up to GJ_THREADS unknowns, else two

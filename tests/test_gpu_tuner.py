@@ -1,5 +1,5 @@
-"""The slab-inverse autotuner of the interface solve: a handle measures both
-variants on its first solve, writes its choice to the cache named by
+"""The slab-inverse autotuner of the interface solve: a handle measures every
+admissible variant on its first solve, writes its choice to the cache named by
 MRCM_TUNE_CACHE, and a second handle of the same shape class takes the choice
 from the cache and reproduces the first handle's solution bit for bit."""
 import json
@@ -31,12 +31,12 @@ def test_tuning_cache_round_trip(tmp_path, monkeypatch):
     case = I.config_channel2d(n=128, n_smooth=1)
     st1, p1, u1 = _run(case)
     assert st1["slab_inverse_source"] == "measured", st1
-    assert st1["tune_ms"]["gauss-jordan"] > 0 and st1["tune_ms"]["lu"] > 0, st1
+    assert min(st1["tune_ms"].values()) > 0, st1   # all three slab inverses admit 128 x 128
     entries = json.loads(cache.read_text())
     assert len(entries) == 1
     (key, entry), = entries.items()
     assert key.startswith("interface dim2 ") and entry["slab_inverse"] == st1["slab_inverse"], (key, entry)
-    assert entry["gauss_jordan_steps"] > 0 and entry["lu_steps"] > 0
+    assert entry["gauss_jordan_steps"] > 0 and entry["lu_steps"] > 0 and entry["gauss_jordan_registers_steps"] > 0
     st2, p2, u2 = _run(case)
     assert st2["slab_inverse_source"] == "cache" and st2["slab_inverse"] == st1["slab_inverse"], st2
     assert np.array_equal(p1, p2) and np.array_equal(u1, u2)

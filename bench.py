@@ -106,35 +106,43 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic work (counting rule: factor n b^2, solve 4 n b per right-hand side)
 # ---------------------------------------------------------------------------
-def algorithmic_flops(case):
-    """Per phase: FP32/FP64 arithmetic the method needs on this workload (one
-    factorisation per operator, one solve per right-hand side)."""
-    prob, part = case.problem, case.partition
-    n, sub, l = prob.n, part.sub, part.overlap
-    M = [n[a] // sub[a] for a in range(2)]
-    npsi = 2 if case.params.space == 1 else 1
-    basis = 0.0
-    smooth = 0.0
-    for iy in range(M[1]):
-        for ix in range(M[0]):
-            lo = [ix * sub[0], iy * sub[1]]
-            hi = [lo[0] + sub[0], lo[1] + sub[1]]
-            loh = [max(0, lo[a] - l) for a in range(2)]
-            hih = [min(n[a], hi[a] + l) for a in range(2)]
-            bx, by = hih[0] - loh[0], hih[1] - loh[1]
-            nh = bx * by
-            nsides = (ix > 0) + (ix < M[0] - 1) + (iy > 0) + (iy < M[1] - 1)
-            N = nsides * npsi
-            ni = sub[0] * sub[1]
-            basis += nh * bx * bx + N * 4 * nh * bx + ni * sub[0] ** 2 + 4 * ni * sub[0]
-            smooth += 4 * nh * bx
-    # interface: every slab (one layer of subdomains along the last axis) is
-    # inverted once per factorisation, 2 n^3 flops for n unknowns
-    lu = 0.0
-    for iy in range(M[1]):
-        ns = sum(((ix > 0) + (ix < M[0] - 1) + (iy > 0) + (iy < M[1] - 1)) * npsi for ix in range(M[0]))
-        lu += 2.0 * ns ** 3
-    return {"local_basis": basis, "smooth_per_step": smooth, "interface_lu": lu}
+def _band(sides):
+    """Band half-width of a box in natural order with the short axes fastest:
+    the smallest side in 2D, the product of the two smallest in 3D."""
+    s = sorted(sides)
+    return s[0] if len(s) == 2 else s[0] * s[1]
+
+
+def algorithmic_work(cases):
+    """Arithmetic the method needs on these problems (one factorisation per
+    operator, one solve per right-hand side, 2 n^3 per slab inverse):
+    flops of the basis build (basis boxes, particular problems), of one
+    smoothing step, of the slab inverses, and the local right-hand sides."""
+    basis = smooth = slab = 0.0
+    rhs = 0
+    for case in cases:
+        prob, part, pm = case.problem, case.partition, case.params
+        d, n, sub, l = prob.dim, prob.n, part.sub, part.overlap
+        M = [n[a] // sub[a] for a in range(d)]
+        npsi = 1 if pm.space == 0 else (2 if d == 2 else 3)
+        extra = pm.alpha_basis != pm.alpha_smooth   # a second factor of every box for the smoothing
+        ni = int(np.prod(sub))
+        bi = _band(sub)
+        layer = {}
+        for idx in np.ndindex(*M[::-1]):
+            mi = idx[::-1]
+            lo = [mi[a] * sub[a] for a in range(d)]
+            hi = [lo[a] + sub[a] for a in range(d)]
+            sides = [min(n[a], hi[a] + l) - max(0, lo[a] - l) for a in range(d)]
+            nh, bh = int(np.prod(sides)), _band(sides)
+            ns = sum((mi[a] > 0) + (mi[a] < M[a] - 1) for a in range(d))
+            N = ns * npsi
+            basis += nh * bh * bh * (2 if extra else 1) + N * 4 * nh * bh + ni * bi * bi + 4 * ni * bi
+            smooth += 4 * nh * bh
+            rhs += N + 1
+            layer[mi[-1]] = layer.get(mi[-1], 0) + N
+        slab += sum(2.0 * float(k) ** 3 for k in layer.values())
+    return {"local_basis": basis, "smooth_per_step": smooth, "interface_lu": slab, "basis_rhs": rhs}
 
 
 def measured_traffic(kernel):
@@ -156,17 +164,48 @@ def measured_traffic(kernel):
     return rec["bytes_per_launch"] if hsh.hexdigest() == rec["sha256"] else None
 
 
+SLAB_KERNEL = {"gauss-jordan-registers": "k_gjr_inverse", "gauss-jordan": "k_gj_inverse", "lu": "k_lu_inverse"}
+LIMITER = {
+    "local_basis": "latency: the dependent chain of line factorisations and solves of each box (one box per CTA)",
+    "smooth": "latency: one box per CTA, a chain of line solves per sweep, 2^d dependent colour launches",
+    "interface_lu": "latency: the pivot chain (one panel owner at a time) of the slabs of a reduction level",
+}
+
+
+def kernel_rooflines(work, tm, n_smooth, peaks, precision, slab_inverse, dim):
+    """Per kernel group: algorithmic flops per launch / device time per launch
+    against the measured FMA peak of the form's local arithmetic (FP32 for the
+    mixed form, FP64 for the FP64 form; the slab inverses are FP32 in both)."""
+    local_kind = "fp32" if precision == "mixed" else "fp64"
+    tag = "3d" if dim == 3 else "2d"
+    names = {"local_basis": f"k_local{tag}<{'float' if local_kind == 'fp32' else 'double'}>",
+             "smooth": f"k_smooth{tag}<{'float' if local_kind == 'fp32' else 'double'}>",
+             "interface_lu": SLAB_KERNEL.get(slab_inverse, slab_inverse)}
+    total = {"local_basis": work["local_basis"], "smooth": work["smooth_per_step"] * n_smooth,
+             "interface_lu": work["interface_lu"]}
+    out = {}
+    for ph in ("local_basis", "smooth", "interface_lu"):
+        ms, nl = tm.get(ph, (0.0, 0))
+        if ms <= 0 or nl <= 0:
+            continue
+        kind = "fp32" if ph == "interface_lu" else local_kind
+        peak = peaks[kind]
+        per_launch_ms = ms / nl
+        wl = total[ph] / nl
+        ach = wl / (per_launch_ms * 1e-3) / 1e12
+        out[ph] = {"kernel": names[ph], "bound": "alu", "pipe": kind, "achieved": ach, "peak": peak,
+                   "unit": "TFLOP/s", "frac": ach / peak, "ms_per_step": ms, "launches_per_step": nl,
+                   "launch_ms": per_launch_ms, "work_per_launch_flop": wl,
+                   "traffic": measured_traffic(names[ph]), "limiter": LIMITER[ph]}
+    return out
+
+
 def local_solves_per_step(case):
     """Local right-hand sides per step: N_i basis + 1 particular + N_s smoothing per subdomain."""
+    w = algorithmic_work([case])
     n, sub = case.problem.n, case.partition.sub
-    M = [n[a] // sub[a] for a in range(2)]
-    npsi = 2 if case.params.space == 1 else 1
-    tot = 0
-    for iy in range(M[1]):
-        for ix in range(M[0]):
-            nsides = (ix > 0) + (ix < M[0] - 1) + (iy > 0) + (iy < M[1] - 1)
-            tot += nsides * npsi + 1 + N_SMOOTH
-    return tot
+    nsub = int(np.prod([n[a] // sub[a] for a in range(case.problem.dim)]))
+    return w["basis_rhs"] + nsub * N_SMOOTH
 
 
 def sm_count():
@@ -174,11 +213,69 @@ def sm_count():
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
+def measured_peaks(stream):
+    """FP32 / FP64 FMA throughput of this GPU (the library's FMA probe) and
+    the measured figures, if present."""
+    from paper_2404_13811_gb300 import _lib as L
+    f32, f64 = L.mrcm_measure_fma_peaks(stream.cuda_stream)
+    out = {"fp32": f32, "fp64": f64, "unit": "TFLOP/s",
+           "source": "mrcm_measure_fma_peaks: independent FMA chains on every SM, CUDA events, median of 3"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                mp = json.load(fh)
+            out["measured_peaks_json"] = {k: mp[k] for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in mp}
+        except Exception:
+            pass
+    return out
+
+
+class Timer:
+    """Device time of K steps after W warm-up steps, L2 flushed (512 MB write)
+    before every timed step, CUDA events on the launching stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.stream = stream
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def __call__(self, fn, K, W):
+        import torch
+        for _ in range(W):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(K):
+            self.flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.sum(ms)), ms
+
+
+def phase_times(s, step_eager, reps=2):
+    """Per-phase device time and kernel counts per step from eager steps (the
+    kernels the captured graph replays), outside the timed region."""
+    s.profile(True)
+    for _ in range(reps):
+        step_eager(s)
+    tm = {k: (v[0] / reps, v[1] / reps) for k, v in s.timings().items()}
+    s.profile(False)
+    return tm
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args, rank, world):
     import torch
+    from paper_2404_13811_gb300 import _lib as L
     from paper_2404_13811_gb300 import build as B
     from paper_2404_13811_gb300 import inputs as I
     from paper_2404_13811_gb300.solver import MRCM
@@ -186,14 +283,22 @@ def run_gpu(args, rank, world):
     B.build()
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    # the slab-inverse choice is measured once per shape class and tolerance
+    # and then read from the cache, as a long-running user would have it
+    fd, cache = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    os.unlink(cache)
+    os.environ["MRCM_TUNE_CACHE"] = cache
     case = I.config_channel2d()
     prob, part, pm = case.problem, case.partition, case.params
     ncell = prob.ncells
     stream = torch.cuda.current_stream()
+    timer = Timer(stream)
+    peaks = measured_peaks(stream)
 
-    def make(precision, device_inputs=True, tol=1e-12):
+    def make(precision, tol=1e-12):
         return MRCM(prob, part, space=pm.space, alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth,
-                    precision=precision, ir_tol=tol, max_ir=30, stream=stream, device_inputs=device_inputs)
+                    precision=precision, ir_tol=tol, max_ir=30, stream=stream, device_inputs=True)
 
     def step(s):
         # the whole step (basis, interface, smoothing) as one captured CUDA
@@ -205,11 +310,10 @@ def run_gpu(args, rank, world):
         s.solve_interface()
         s.smooth(N_SMOOTH)
 
-    # correctness against the oracle (and the CPU baseline timing) on rank 0
+    ref = None
     cpu = None
-    errs = {}
-    solvers = {"mixed": make("mixed"), "fp64": make("fp64")}
-    if rank == 0 and not args.no_oracle:
+    use_oracle = rank == 0 and not args.no_oracle
+    if use_oracle:
         from oracle import mrcm_oracle as O
         t0 = time.perf_counter()
         ref = O.mrcm_os(prob, part.sub, part.overlap, pm.space, pm.alpha_basis, pm.alpha_smooth, N_SMOOTH)
@@ -217,132 +321,116 @@ def run_gpu(args, rank, world):
         cpu = {"value": ncell / t_cpu, "unit": "cells/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"one full pass of the oracle on the whole {WORKLOAD} workload "
                          f"({t_cpu:.1f} s; numpy/scipy, LAPACK threads = host cores)"}
-        for name, s in solvers.items():
-            step(s)
-            p, u = s.fluxes()
-            ep, eu = O.rel_errors(prob, p, u, ref.p, ref.u)
-            errs[name] = {"flux_rel_l2": eu, "pressure_rel_l2": ep}
-    # the equal-error comparison: the mixed form with the refinement tolerance
-    # tightened towards the FP64 form's flux error (the first tolerance whose
-    # local and interface refinements converge)
-    from paper_2404_13811_gb300 import _lib as L
-    eq = {"note": "mixed form with ir_tol tightened towards the FP64 form's flux error"}
-    for tol in (1e-14, 1e-13):
-        s_eq = None
-        try:
-            s_eq = make("mixed", tol=tol)
-            step(s_eq)
-            eq["ir_tol"] = tol
-            if rank == 0 and not args.no_oracle:
-                p, u = s_eq.fluxes()
-                ep, eu = O.rel_errors(prob, p, u, ref.p, ref.u)
-                eq["flux_rel_l2"], eq["pressure_rel_l2"] = eu, ep
-            solvers["mixed_eq"] = s_eq
-            break
-        except L.MrcmError as exc:
-            eq["unconverged_at_" + f"{tol:.0e}"] = str(exc)
-            if s_eq is not None:
-                s_eq.close()
 
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
+    def errors(s):
+        if ref is None:
+            return None
+        p, u = s.fluxes()
+        ep, eu = O.rel_errors(prob, p, u, ref.p, ref.u)
+        return {"flux_rel_l2": eu, "pressure_rel_l2": ep}
 
-    def timed(s, K, W, profile=False):
-        for _ in range(W):
-            step(s)
-        torch.cuda.synchronize()
-        if profile:
-            s.profile(True)
-        tot = 0.0
-        for k in range(K):
-            flush.fill_(float(k))
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(s)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        tm = None
-        if profile:
-            # per-phase device time and kernel counts from eager steps (the
-            # same kernels the graph replays), outside the timed region
-            s.profile(True)
-            for _ in range(2):
-                step_eager(s)
-            tm = {k: (v[0] / 2, v[1] / 2) for k, v in s.timings().items()}
-            s.profile(False)
-        return tot, tm
+    solvers = {"mixed": make("mixed"), "fp64": make("fp64")}
+    errs = {}
+    for name, s in solvers.items():
+        step(s)
+        errs[name] = errors(s)
 
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(dev)
     clk.start()
-    ms_mixed, tm = timed(solvers["mixed"], args.steps, args.warmup, profile=True)
+    ms_mixed, _ = timer(lambda: step(solvers["mixed"]), args.steps, args.warmup)
+    k64 = max(3, args.steps // 4)
+    ms_fp64, _ = timer(lambda: step(solvers["fp64"]), k64, 1)
+
+    # the fixed-error comparison: both forms over a range of ir_tol (the
+    # interface refinement of both and the local refinement of the mixed
+    # form stop there); at the tightest flux error both reach, and at 1e-10,
+    # each form at its fastest setting that meets the target
+    sweep = {"mixed": [], "fp64": []}
+    tols = {"mixed": (1e-10, 1e-11, 1e-12, 1e-13), "fp64": (1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13)}
+    ks = max(3, args.steps // 4)
+    for form in ("mixed", "fp64"):
+        for tol in tols[form]:
+            rec = {"ir_tol": tol}
+            s = None
+            try:
+                s = make(form, tol)
+                step(s)
+                rec.update(errors(s) or {})
+                t, _ = timer(lambda: step(s), ks, 1)
+                rec["ms_per_step"] = t / ks
+            except L.MrcmError as exc:
+                rec["error"] = str(exc)
+            if s is not None:
+                s.close()
+            sweep[form].append(rec)
     clocks = clk.stop()
-    ms_fp64, _ = timed(solvers["fp64"], max(2, args.steps // 4), 1)
-    if "mixed_eq" in solvers:
-        ms_eq, _ = timed(solvers["mixed_eq"], max(2, args.steps // 4), 1)
-        eq["ms_per_step"] = ms_eq / max(2, args.steps // 4)
-        eq["value"] = ncell / (eq["ms_per_step"] * 1e-3)
-        eq["unit"] = "cells/s"
+    clocks["window"] = "sampled over the timed steps of both forms and of the ir_tol sweep"
+
+    fixed = None
+    if use_oracle:
+        ok = {f: [r for r in sweep[f] if "ms_per_step" in r and "flux_rel_l2" in r] for f in sweep}
+        if ok["mixed"] and ok["fp64"]:
+            tight = max(min(r["flux_rel_l2"] for r in ok[f]) for f in ok)
+            fixed = []
+            for target in sorted({tight, 1e-10}):
+                entry = {"target_flux_rel_l2": target}
+                for f in ok:
+                    meet = [r for r in ok[f] if r["flux_rel_l2"] <= target * (1 + 1e-9)]
+                    if meet:
+                        b = min(meet, key=lambda r: r["ms_per_step"])
+                        entry[f] = dict(b, value=ncell / (b["ms_per_step"] * 1e-3), unit="cells/s")
+                if "mixed" in entry and "fp64" in entry:
+                    entry["speedup_mixed_over_fp64"] = entry["fp64"]["ms_per_step"] / entry["mixed"]["ms_per_step"]
+                fixed.append(entry)
+
     torch.cuda.synchronize()
     ms_mixed = max_over_ranks(ms_mixed, world, "cuda")
     ms_step = ms_mixed / args.steps
     value = ncell * world / (ms_step * 1e-3)
-    fp64_value = ncell / (ms_fp64 / max(2, args.steps // 4) * 1e-3)
+    fp64_ms = ms_fp64 / k64
 
-    # end to end through the C ABI from pinned host memory, result read back
-    Kh = torch.from_numpy(np.ascontiguousarray(prob.K)).pin_memory()
-    fh = torch.from_numpy(np.ascontiguousarray(prob.f)).pin_memory()
+    # per-kernel rooflines (phase device times from eager steps of the same
+    # kernels), and the dominant kernel of the mixed form as the headline
+    tm = phase_times(solvers["mixed"], step_eager)
+    tm64 = phase_times(solvers["fp64"], step_eager)
+    st = solvers["mixed"].stats()
+    st64 = solvers["fp64"].stats()
+    work = algorithmic_work([case])
+    kr = kernel_rooflines(work, tm, N_SMOOTH, peaks, "mixed", st["slab_inverse"], 2)
+    kr64 = kernel_rooflines(work, tm64, N_SMOOTH, peaks, "fp64", st64["slab_inverse"], 2)
+    dom = max(kr, key=lambda k: kr[k]["ms_per_step"])
+    roof = {k: kr[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "pipe",
+                                    "launch_ms", "work_per_launch_flop", "limiter")}
+    roof["peak_basis"] = "of measured: FMA probe (mrcm_measure_fma_peaks) on this GPU"
+    roof["work_rule"] = "factor n b^2 and 4 n b per right-hand side (local kernels); 2 n^3 per slab inverse"
+
+    # end to end through the C ABI, host buffers: every step a new K from
+    # pinned host memory (mrcm_set_permeability copies it), the whole method
+    # (mrcm_run, eager: a new operator), and p, u read back to pinned memory
+    Kh = torch.from_numpy(np.ascontiguousarray(prob.K).reshape(-1)).pin_memory()
     pout = torch.empty(ncell, dtype=torch.float64).pin_memory()
     uout = torch.empty((ncell, 4), dtype=torch.float64).pin_memory()
-    from paper_2404_13811_gb300 import _lib as L
-    g, b, pt = L.make_structs(2, prob.n, prob.h, prob.bc_kind, prob.bc_value, part.sub, part.overlap)
-    prm = L.make_params(pm.space, pm.alpha_basis, pm.alpha_smooth, L.MRCM_MIXED, 1e-12, 8)
-    ke = max(2, args.steps // 4)
+    s_e = make("mixed")
     e2e_ms = 0.0
+    ke = max(3, args.steps // 4)
     for k in range(ke + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = L.mrcm_create(g, Kh.data_ptr(), fh.data_ptr(), b, pt, prm, 0, stream.cuda_stream)
-        L.mrcm_build_basis(h)
-        L.mrcm_solve_interface(h)
-        L.mrcm_smooth(h, N_SMOOTH)
-        L.mrcm_fluxes(h, 0, uout.numpy(), pout.numpy())
+        L.mrcm_set_permeability(s_e.h, Kh.numpy(), 0)
+        L.mrcm_run(s_e.h, N_SMOOTH, 0)
+        L.mrcm_fluxes(s_e.h, 0, uout.numpy(), pout.numpy())
         dt = time.perf_counter() - t0
-        L.mrcm_destroy(h)
         if k > 0:
             e2e_ms += dt * 1e3
+    s_e.close()
     e2e = {"value": ncell / (e2e_ms / ke * 1e-3), "unit": "cells/s",
-           "h2d_bytes_per_step": int(2 * ncell * 8), "d2h_bytes_per_step": int(5 * ncell * 8),
-           "includes": "create (plan, allocation, H2D of K and f) + build + interface + 8 smoothing steps + D2H of p, u"}
+           "h2d_bytes_per_step": int(ncell * 8), "d2h_bytes_per_step": int(5 * ncell * 8),
+           "includes": "mrcm_set_permeability (H2D of K, face coefficients) + mrcm_run eager (basis, interface "
+                       "with the cached slab-inverse choice, 8 smoothing steps) + mrcm_fluxes (D2H of p, u)"}
 
-    # roofline of the dominant kernel: the one with the most device time per
-    # step among the local basis kernels, the smoothing kernel and the slab LU
-    flops = algorithmic_flops(case)
-    nsm = sm_count()
-    mhz = clocks.get("sm_mhz") or 1485.0
-    peak32 = nsm * 128 * 2 * mhz * 1e6 / 1e12
-    phase_ms = {k: v[0] for k, v in tm.items()}
-    launches = {k: v[1] for k, v in tm.items()}
-    dom = max(("local_basis", "smooth", "interface_lu"), key=lambda k: phase_ms[k])
-    total = {"local_basis": flops["local_basis"], "smooth": flops["smooth_per_step"] * N_SMOOTH,
-             "interface_lu": flops["interface_lu"]}[dom]
-    kname = {"local_basis": "k_local2d<float>", "smooth": "k_smooth2d<float>", "interface_lu": "k_lu_inverse"}[dom]
-    work = total / max(launches[dom], 1)
-    per_launch_ms = phase_ms[dom] / max(launches[dom], 1)
-    achieved = work / (per_launch_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": kname,
-            "achieved": achieved, "peak": peak32, "unit": "TFLOP/s", "frac": achieved / peak32,
-            "traffic": measured_traffic(kname),
-            "peak_basis": f"{nsm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (median sampled SM clock; "
-                          "MEASURED_PEAKS.json holds no FP32 SIMT figure)",
-            "work_per_launch_flop": work, "launch_ms": per_launch_ms,
-            "work_rule": "factor n b^2 and 4 n b per solve (local kernels); 2 n^3 per slab inverse"}
-    # kernels of one step (the captured graph replays the eager sequence; the
-    # slab-LU phase is a part of interface_factor)
     gpu_launches = int(round(sum(v[1] for k, v in tm.items() if k not in ("graph", "interface_lu"))))
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
@@ -350,13 +438,19 @@ def run_gpu(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [512, 512], "subdomains": [32, 32], "sub": [16, 16],
                    "overlap": 4, "space": "P1", "n_smooth": N_SMOOTH, "alpha": 1.0,
-                   "contrast": 1e4, "precision": "mixed (FP32 local factor/solves, FP64 residuals)",
+                   "contrast": 1e4, "precision": "mixed (FP32 local factor/solves, FP64 residuals), ir_tol 1e-12",
                    "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas{world}",
                    "step": "mrcm_run: the whole step replayed as one captured CUDA graph"},
-        "fp64_form": {"value": fp64_value, "unit": "cells/s", "ms_per_step": 1e3 * ncell / fp64_value},
-        "mixed_equal_error": eq,
-        "errors_vs_oracle": errs, "phase_ms_per_step": phase_ms, "launches_per_step": launches,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
+        "fp64_form": {"value": ncell / (fp64_ms * 1e-3), "unit": "cells/s", "ms_per_step": fp64_ms,
+                      "form": "FP64 local factorisations and solves; the interface solve is the same in both "
+                              "forms (FP32 block-cyclic-reduction factors, FP64 residuals and refinement)"},
+        "fixed_error_comparison": fixed, "ir_tol_sweep": sweep,
+        "errors_vs_oracle": errs, "phase_ms_per_step": {k: v[0] for k, v in tm.items()},
+        "launches_per_step": {k: v[1] for k, v in tm.items()},
+        "fp64_phase_ms_per_step": {k: v[0] for k, v in tm64.items()},
+        "roofline": roof, "kernel_rooflines": {"mixed": kr, "fp64": kr64}, "peaks": peaks,
+        "stats": {"mixed": st, "fp64": st64},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
         "subdomain_solves_per_s": local_solves_per_step(case) * world / (ms_step * 1e-3),
     }
     for s in solvers.values():
@@ -366,7 +460,7 @@ def run_gpu(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-# timing lines of the other workloads (not the benchmark line)
+# lines of the other workloads (not the benchmark line)
 # ---------------------------------------------------------------------------
 def run_other(args):
     import torch
@@ -375,53 +469,74 @@ def run_other(args):
     from paper_2404_13811_gb300.solver import MRCM
 
     B.build()
+    fd, cache = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    os.unlink(cache)
+    os.environ["MRCM_TUNE_CACHE"] = cache
     stream = torch.cuda.current_stream()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
-
-    def timeit(fn, K, W):
-        for _ in range(W):
-            fn()
-        torch.cuda.synchronize()
-        tot = 0.0
-        for k in range(K):
-            flush.fill_(float(k))
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        return tot / K
-
-    def phases(s, ns):
-        s.profile(True)
-        s.build_basis()
-        s.solve_interface()
-        s.smooth(ns)
-        tm = s.timings()
-        s.profile(False)
-        return {k: round(v[0], 3) for k, v in tm.items() if v[0] > 0}
+    timer = Timer(stream)
+    peaks = measured_peaks(stream)
+    dev = torch.cuda.current_device()
 
     w = args.workload
     line = {"workload": w, "unit": "cells/s", "steps": args.steps, "warmup": args.warmup,
-            "l2": "flushed (512 MB write) between timed steps", "data": "synthetic"}
+            "l2": "flushed (512 MB write) between timed steps", "data": "synthetic", "peaks": peaks}
     if w in ("small", "layered3d", "ensemble"):
         cases = I.config_ensemble() if w == "ensemble" else [I.config_small() if w == "small" else I.config_layered3d()]
         probs = [c.problem for c in cases]
         parts = [c.partition for c in cases]
         pm = cases[0].params
         cells = sum(p.ncells for p in probs)
+        dim = probs[0].dim
         line.update({"members": len(cases), "cells": cells, "n_smooth": pm.n_smooth,
                      "step": "mrcm_run: the whole step replayed as one captured CUDA graph"})
+        # oracle check: every member of the small and 3D workloads; a seeded
+        # subset of 4 members of the ensemble
+        check = list(range(len(cases)))
+        if w == "ensemble":
+            check = sorted(np.random.default_rng(4040).choice(len(cases), 4, replace=False).tolist())
+        refs = {}
+        if not args.no_oracle:
+            from oracle import mrcm_oracle as O
+            t0 = time.perf_counter()
+            for m in check:
+                c = cases[m]
+                refs[m] = O.mrcm_os(c.problem, c.partition.sub, c.partition.overlap, c.params.space,
+                                    c.params.alpha_basis, c.params.alpha_smooth, c.params.n_smooth)
+            line["oracle"] = {"members_checked": check, "seconds": time.perf_counter() - t0,
+                              "subset": "seeded subset of 4 members" if w == "ensemble" else "all members"}
+        work = algorithmic_work(cases)
+        clk = Clocks(dev)
+        clk.start()
         for precision in ("mixed", "fp64"):
             s = MRCM(probs if len(probs) > 1 else probs[0], parts if len(parts) > 1 else parts[0], space=pm.space,
                      alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth, precision=precision, stream=stream)
-            ms = timeit(lambda: s.run(pm.n_smooth, graph=True), args.steps, args.warmup)
-            line[precision] = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "phase_ms_eager": phases(s, pm.n_smooth),
-                               "subdomains": s.stats()["subdomains"]}
+            s.run(pm.n_smooth, graph=True)
+            tot, _ = timer(lambda: s.run(pm.n_smooth, graph=True), args.steps, args.warmup)
+            ms = tot / args.steps
+            errs = {}
+            if refs:
+                worst = [0.0, 0.0]
+                for m in check:
+                    p, u = s.fluxes(member=m)
+                    ep, eu = O.rel_errors(cases[m].problem, p, u, refs[m].p, refs[m].u)
+                    worst = [max(worst[0], eu), max(worst[1], ep)]
+                errs = {"flux_rel_l2_max": worst[0], "pressure_rel_l2_max": worst[1]}
+
+            def eager(sv):
+                sv.build_basis()
+                sv.solve_interface()
+                sv.smooth(pm.n_smooth)
+
+            tm = phase_times(s, eager, reps=1)
+            st = s.stats()
+            kr = kernel_rooflines(work, tm, pm.n_smooth, peaks, precision, st["slab_inverse"], dim)
+            dom = max(kr, key=lambda k: kr[k]["ms_per_step"])
+            line[precision] = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "errors_vs_oracle": errs,
+                               "phase_ms_eager": {k: round(v[0], 3) for k, v in tm.items() if v[0] > 0},
+                               "roofline": kr[dom], "kernel_rooflines": kr, "stats": st}
             s.close()
+        line["clocks"] = clk.stop()
     else:
         case = I.config_adjoint()
         prob, part, pm = case.problem, case.partition, case.params
@@ -433,6 +548,19 @@ def run_other(args):
         t.close()
         line.update({"cells": prob.ncells, "n_smooth": pm.n_smooth,
                      "loss": "sum over the 4 faces of 8 sink cells of (u - u_target)^2"})
+        gref = None
+        if not args.no_oracle:
+            from oracle import mrcm_adjoint as OA
+            from oracle import mrcm_oracle as O
+            t0 = time.perf_counter()
+            ref = O.mrcm_os(prob, part.sub, part.overlap, pm.space, pm.alpha_basis, pm.alpha_smooth, pm.n_smooth)
+            gu = np.zeros_like(ref.u)
+            gu[sinks] = 2.0 * (ref.u[sinks] - ut.cpu().numpy())
+            _, gref = OA.mrcm_os_adjoint(prob, part.sub, part.overlap, pm.space, pm.alpha_basis, pm.alpha_smooth,
+                                         pm.n_smooth, np.zeros(prob.ncells), gu)
+            line["oracle"] = {"seconds": time.perf_counter() - t0, "what": "forward pass and adjoint gradient"}
+        clk = Clocks(dev)
+        clk.start()
         for precision in ("mixed", "fp64"):
             s = MRCM(prob, part, space=pm.space, alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth,
                      precision=precision, stream=stream)
@@ -448,11 +576,19 @@ def run_other(args):
                 return s.adjoint(None, gu)
 
             fwd()
-            ms_f = timeit(fwd, args.steps, args.warmup)
-            ms_g = timeit(grad, args.steps, args.warmup)
-            line[precision] = {"forward_ms": ms_f, "adjoint_ms": ms_g, "adjoint_over_forward": ms_g / ms_f,
-                               "value": prob.ncells / ((ms_f + ms_g) * 1e-3)}
+            ms_f, _ = timer(fwd, args.steps, args.warmup)
+            ms_g, _ = timer(grad, args.steps, args.warmup)
+            ms_f /= args.steps
+            ms_g /= args.steps
+            rec = {"forward_ms": ms_f, "adjoint_ms": ms_g, "adjoint_over_forward": ms_g / ms_f,
+                   "value": prob.ncells / ((ms_f + ms_g) * 1e-3)}
+            if gref is not None:
+                fwd()
+                g = grad().cpu().numpy()
+                rec["gradient_rel_l2_vs_oracle"] = float(np.linalg.norm(g - gref) / np.linalg.norm(gref))
+            line[precision] = rec
             s.close()
+        line["clocks"] = clk.stop()
     print(json.dumps(line), flush=True)
 
 

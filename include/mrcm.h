@@ -265,7 +265,15 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
  * the LU.  With the environment variable MRCM_TUNE_CACHE naming a JSON file,
  * the choice is read from it by shape class (dimension, slab size, slab and
  * level counts, members, precision, space, ir_tol) when present and written to
- * it after a measurement. */
+ * it after a measurement.
+ *
+ * Per-call metrics.  With the environment variable MRCM_METRICS naming a file
+ * (or "stderr"), every outermost call among mrcm_build_basis,
+ * mrcm_solve_interface, mrcm_smooth, mrcm_run and mrcm_adjoint appends one
+ * JSON line to it: the call, its return code, its host wall time in ms (the
+ * calls synchronise, so this includes their device work), the counters above
+ * and the slab-inverse choice with its source and measured times.  Calls made
+ * inside mrcm_run write no line of their own. */
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl);
 
 /* Device-time profiling of the calls above.  enable = 1 starts recording a

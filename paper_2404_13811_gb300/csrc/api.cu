@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -183,6 +185,7 @@ struct mrcm_handle {
     double* d_kry = nullptr;      // its workspace (allocated on first use)
     int loc_ir = 0;
     long long local_solves = 0;
+    int call_depth = 0;           // nesting of public calls (the metrics line is written by the outermost)
 };
 
 namespace {
@@ -978,6 +981,48 @@ static int solve_interface_T(mrcm_handle* h) {
     return 0;
 }
 
+// Per-call metrics: with the environment variable MRCM_METRICS naming a file
+// (or "stderr"), every outermost call of the solve path appends one JSON line
+// with its host wall time, return code, the refinement counts and residual,
+// and the slab-inverse choice of the autotuner.
+static const char* const kSlabNamesLog[3] = {"gauss-jordan", "lu", "gauss-jordan-registers"};
+
+struct CallLog {
+    mrcm_handle* h;
+    const char* name;
+    const int* rc;
+    std::chrono::steady_clock::time_point t0;
+    CallLog(mrcm_handle* hh, const char* nm, const int* r) : h(hh), name(nm), rc(r), t0(std::chrono::steady_clock::now()) {
+        ++h->call_depth;
+    }
+    ~CallLog() {
+        if (--h->call_depth > 0) return;
+        const char* path = std::getenv("MRCM_METRICS");
+        if (!path || !*path) return;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        const int v = h->slab_variant;
+        char buf[768];
+        snprintf(buf, sizeof(buf),
+                 "{\"call\": \"%s\", \"rc\": %d, \"wall_ms\": %.4f, \"subdomains\": %zu, \"interface_unknowns\": %d, "
+                 "\"interface_ir_steps\": %d, \"interface_residual\": %.3e, \"interface_gmres\": %s, "
+                 "\"local_ir_steps_max\": %d, \"local_solves\": %lld, \"smooth_steps\": %d, \"slab_inverse\": \"%s\", "
+                 "\"slab_inverse_source\": \"%s\", \"tune_ms\": {\"gauss-jordan\": %.4f, \"lu\": %.4f, "
+                 "\"gauss-jordan-registers\": %.4f}}\n",
+                 name, *rc, ms, h->sub.size(), h->nif, h->if_iters, h->if_res, h->if_krylov ? "true" : "false",
+                 h->loc_ir, h->local_solves, h->smooth_steps, v >= 0 && v < 3 ? kSlabNamesLog[v] : "none",
+                 h->tune_source == 1 ? "cache" : h->tune_source == 2 ? "measured" : "fixed", h->tune_ms[0],
+                 h->tune_ms[1], h->tune_ms[2]);
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lock(mu);
+        if (std::strcmp(path, "stderr") == 0) {
+            std::fputs(buf, stderr);
+        } else if (FILE* f = std::fopen(path, "a")) {
+            std::fputs(buf, f);
+            std::fclose(f);
+        }
+    }
+};
+
 extern "C" {
 
 int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
@@ -994,7 +1039,7 @@ int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
     return create_impl(count, grids, K, f, bcs, parts, params, device_ptrs, cuda_stream, out);
 }
 
-int mrcm_build_basis(mrcm_handle* h) {
+static int build_basis_body(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     h->err.clear();
     h->stage = ST_CREATED;
@@ -1005,6 +1050,14 @@ int mrcm_build_basis(mrcm_handle* h) {
     for (auto& sd : h->sub) h->local_solves += sd.nbasis + 1;
     h->stage = ST_BASIS;
     return 0;
+}
+
+int mrcm_build_basis(mrcm_handle* h) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    int rc = 0;
+    CallLog log(h, "mrcm_build_basis", &rc);
+    rc = build_basis_body(h);
+    return rc;
 }
 
 // The interface refinement's target (relative, row-equilibrated max norm).
@@ -1284,7 +1337,7 @@ static void tune_cache_store(const std::string& key, int variant, const double* 
     std::rename(tmp.c_str(), path);
 }
 
-int mrcm_solve_interface(mrcm_handle* h) {
+static int solve_interface_body(mrcm_handle* h) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_BASIS) return fail(h, MRCM_ERR_STATE, "mrcm_solve_interface must follow mrcm_build_basis");
     h->err.clear();
@@ -1369,7 +1422,15 @@ int mrcm_solve_interface(mrcm_handle* h) {
     return 0;
 }
 
-int mrcm_smooth(mrcm_handle* h, int n_steps) {
+int mrcm_solve_interface(mrcm_handle* h) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    int rc = 0;
+    CallLog log(h, "mrcm_solve_interface", &rc);
+    rc = solve_interface_body(h);
+    return rc;
+}
+
+static int smooth_body(mrcm_handle* h, int n_steps) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_smooth must follow mrcm_solve_interface");
     if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
@@ -1380,7 +1441,15 @@ int mrcm_smooth(mrcm_handle* h, int n_steps) {
     return check_status(h);
 }
 
-int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
+int mrcm_smooth(mrcm_handle* h, int n_steps) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    int rc = 0;
+    CallLog log(h, "mrcm_smooth", &rc);
+    rc = smooth_body(h, n_steps);
+    return rc;
+}
+
+static int run_body(mrcm_handle* h, int n_steps, int use_graph) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (n_steps < 0) return fail(h, MRCM_ERR_BAD_INPUT, "n_steps must be >= 0");
     h->err.clear();
@@ -1461,6 +1530,14 @@ int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
     return 0;
 }
 
+int mrcm_run(mrcm_handle* h, int n_steps, int use_graph) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    int rc = 0;
+    CallLog log(h, "mrcm_run", &rc);
+    rc = run_body(h, n_steps, use_graph);
+    return rc;
+}
+
 int mrcm_fluxes(mrcm_handle* h, int member, double* u_cellfaces, double* p_cells, int device_ptrs) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "no solution yet");
@@ -1536,7 +1613,7 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
     return mrcm_adjoint(h, dL_dp, dL_du, dL_dlogK, 0);
 }
 
-int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs) {
+static int adjoint_body(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs) {
     if (!h) return MRCM_ERR_BAD_INPUT;
     if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_adjoint needs a solution");
@@ -1626,6 +1703,14 @@ int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_l
     if (!device_ptrs)
         CUDA_TRY(h, cudaMemcpyAsync(g_logK, W.gout, sizeof(double) * cells, cudaMemcpyDeviceToHost, st));
     return check_status(h);
+}
+
+int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs) {
+    if (!h) return MRCM_ERR_BAD_INPUT;
+    int rc = 0;
+    CallLog log(h, "mrcm_adjoint", &rc);
+    rc = adjoint_body(h, gp, gu, g_logK, device_ptrs);
+    return rc;
 }
 
 int mrcm_stats(const mrcm_handle* h, int* ints, int nints, double* dbl, int ndbl) {

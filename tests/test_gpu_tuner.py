@@ -40,3 +40,29 @@ def test_tuning_cache_round_trip(tmp_path, monkeypatch):
     st2, p2, u2 = _run(case)
     assert st2["slab_inverse_source"] == "cache" and st2["slab_inverse"] == st1["slab_inverse"], st2
     assert np.array_equal(p1, p2) and np.array_equal(u1, u2)
+
+
+def test_metrics_line_per_outermost_call(tmp_path, monkeypatch):
+    """MRCM_METRICS: one JSON line per outermost solve-path call, with the
+    refinement counters and the slab-inverse choice; mrcm_run's inner calls
+    write none."""
+    log = tmp_path / "metrics.jsonl"
+    monkeypatch.setenv("MRCM_METRICS", str(log))
+    monkeypatch.delenv("MRCM_TUNE_CACHE", raising=False)
+    from paper_2404_13811_gb300.solver import MRCM
+    case = I.config_channel2d(n=128, n_smooth=1)
+    pm = case.params
+    s = MRCM(case.problem, case.partition, space=pm.space, alpha_basis=pm.alpha_basis,
+             alpha_smooth=pm.alpha_smooth, precision="mixed")
+    s.run(1)
+    s.build_basis()
+    s.solve_interface()
+    s.smooth(2)
+    s.close()
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [x["call"] for x in lines] == ["mrcm_run", "mrcm_build_basis", "mrcm_solve_interface", "mrcm_smooth"]
+    assert all(x["rc"] == 0 and x["wall_ms"] > 0 for x in lines)
+    si = lines[2]
+    assert si["interface_ir_steps"] > 0 and 0 < si["interface_residual"] <= 1e-9, si
+    assert si["slab_inverse"] in ("gauss-jordan", "lu", "gauss-jordan-registers") and si["subdomains"] == 64
+    assert lines[3]["smooth_steps"] == 2

@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle check and CPU baseline")
+    ap.add_argument("--grid", default=None,
+                    help="layered3d only: cells per axis as nx,ny,nz (default 60,220,85; the layer split "
+                         "keeps its share of the z extent)")
     ap.add_argument("--workload", default="channel2d",
                     choices=["channel2d", "small", "layered3d", "ensemble", "adjoint"],
                     help="channel2d: the benchmark line; the others print a timing line for another "
@@ -240,12 +243,14 @@ class Timer:
         self.stream = stream
         self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def __call__(self, fn, K, W):
+    def __call__(self, fn, K, W, nvtx=None):
         import torch
         for _ in range(W):
             fn()
         torch.cuda.synchronize()
         ms = []
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)   # lets a profiler keep to the timed steps
         for k in range(K):
             self.flush.fill_(float(k))
             torch.cuda.synchronize()
@@ -256,6 +261,8 @@ class Timer:
             e1.record(self.stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
         return float(np.sum(ms)), ms
 
 
@@ -284,11 +291,13 @@ def run_gpu(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     # the slab-inverse choice is measured once per shape class and tolerance
-    # and then read from the cache, as a long-running user would have it
-    fd, cache = tempfile.mkstemp(suffix=".json")
-    os.close(fd)
-    os.unlink(cache)
-    os.environ["MRCM_TUNE_CACHE"] = cache
+    # and then read from the cache, as a long-running user would have it (a
+    # cache named by MRCM_TUNE_CACHE is used as it is)
+    if not os.environ.get("MRCM_TUNE_CACHE"):
+        fd, cache = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        os.unlink(cache)
+        os.environ["MRCM_TUNE_CACHE"] = cache
     case = I.config_channel2d()
     prob, part, pm = case.problem, case.partition, case.params
     ncell = prob.ncells
@@ -340,7 +349,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     clk = Clocks(dev)
     clk.start()
-    ms_mixed, _ = timer(lambda: step(solvers["mixed"]), args.steps, args.warmup)
+    ms_mixed, _ = timer(lambda: step(solvers["mixed"]), args.steps, args.warmup, nvtx="mrcm_timed_steps")
     k64 = max(3, args.steps // 4)
     ms_fp64, _ = timer(lambda: step(solvers["fp64"]), k64, 1)
 
@@ -351,7 +360,7 @@ def run_gpu(args, rank, world):
     sweep = {"mixed": [], "fp64": []}
     tols = {"mixed": (1e-10, 1e-11, 1e-12, 1e-13), "fp64": (1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13)}
     ks = max(3, args.steps // 4)
-    for form in ("mixed", "fp64"):
+    for form in (("mixed", "fp64") if use_oracle else ()):   # the sweep is there for its errors
         for tol in tols[form]:
             rec = {"ir_tol": tol}
             s = None
@@ -367,7 +376,7 @@ def run_gpu(args, rank, world):
                 s.close()
             sweep[form].append(rec)
     clocks = clk.stop()
-    clocks["window"] = "sampled over the timed steps of both forms and of the ir_tol sweep"
+    clocks["window"] = "sampled over the timed steps of both forms (and of the ir_tol sweep with the oracle)"
 
     fixed = None
     if use_oracle:
@@ -469,10 +478,11 @@ def run_other(args):
     from paper_2404_13811_gb300.solver import MRCM
 
     B.build()
-    fd, cache = tempfile.mkstemp(suffix=".json")
-    os.close(fd)
-    os.unlink(cache)
-    os.environ["MRCM_TUNE_CACHE"] = cache
+    if not os.environ.get("MRCM_TUNE_CACHE"):
+        fd, cache = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        os.unlink(cache)
+        os.environ["MRCM_TUNE_CACHE"] = cache
     stream = torch.cuda.current_stream()
     timer = Timer(stream)
     peaks = measured_peaks(stream)
@@ -482,7 +492,12 @@ def run_other(args):
     line = {"workload": w, "unit": "cells/s", "steps": args.steps, "warmup": args.warmup,
             "l2": "flushed (512 MB write) between timed steps", "data": "synthetic", "peaks": peaks}
     if w in ("small", "layered3d", "ensemble"):
-        cases = I.config_ensemble() if w == "ensemble" else [I.config_small() if w == "small" else I.config_layered3d()]
+        if w == "layered3d" and args.grid:
+            n3 = tuple(int(v) for v in args.grid.split(","))
+            cases = [I.config_layered3d(n=n3, n_upper=max(1, round(35 * n3[2] / 85)))]
+            line["grid"] = list(n3)
+        else:
+            cases = I.config_ensemble() if w == "ensemble" else [I.config_small() if w == "small" else I.config_layered3d()]
         probs = [c.problem for c in cases]
         parts = [c.partition for c in cases]
         pm = cases[0].params

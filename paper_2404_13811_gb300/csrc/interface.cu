@@ -29,6 +29,15 @@ constexpr int PUB_FLOATS = 2 * PUB_PAR;        // both parities
 
 
 
+// Programmatic dependent launch: the kernels of the refinement loop are
+// launched so that each may be scheduled while its predecessor drains; each
+// waits for its predecessor's completion (and memory) before touching data,
+// and lets its own successor be scheduled as soon as all its CTAs run.
+__device__ __forceinline__ void pdl_wait_and_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
     // non-negative doubles order like their bit patterns
     atomicMax(a, (unsigned long long)__double_as_longlong(v));
@@ -371,6 +380,7 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
 // Solve phase (per refinement step).
 // ---------------------------------------------------------------------------
 __global__ void k_if_residual(IfPtrs I, const int* row_member, int nrows, int first) {
+    pdl_wait_and_release();
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= nrows) return;
     const double* gv = I.Gv + (size_t)row * 2 * I.NB;
@@ -409,6 +419,7 @@ constexpr int SW_T = 256;
 // forward: y_j = Dinv_j b_j (stored in place), then push into the neighbours:
 // b_jm[mrows] -= Rup y_j, b_jp[vrows] -= Rdn y_j.
 __global__ void __launch_bounds__(SW_T) k_bcr_fwd(IfPtrs I, const ElimDev* el, int nel) {
+    pdl_wait_and_release();
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int e = blockIdx.x / SW_CL;   // the grid is nel clusters
@@ -475,6 +486,7 @@ __global__ void __launch_bounds__(SW_T) k_bcr_fwd(IfPtrs I, const ElimDev* el, i
 // chunks, gathered through distributed shared memory), the products with
 // the inverse columns by chunks of those columns, the final sum by rows.
 __global__ void __launch_bounds__(SW_T) k_bcr_bwd(IfPtrs I, const ElimDev* el, int nel) {
+    pdl_wait_and_release();
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int e = blockIdx.x / SW_CL;
@@ -544,6 +556,7 @@ __global__ void __launch_bounds__(SW_T) k_bcr_bwd(IfPtrs I, const ElimDev* el, i
 }
 
 __global__ void k_if_update(IfPtrs I, int ncols) {
+    pdl_wait_and_release();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncols) return;
     I.x[c] += I.Cs[c] * (double)I.bq[c];
@@ -704,19 +717,21 @@ cudaError_t if_residualT(const IfPtrs& I, const SubDev* sub, const int* col_item
 }
 
 static cudaError_t launch_cluster(const void* kern, int nblocks, int threads, size_t smem, cudaStream_t s,
-                                  void** args, int cl = GJ_CL) {
+                                  void** args, int cl = GJ_CL, bool pdl = false) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblocks);
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cudaLaunchKernelExC(&cfg, kern, args);
 }
 
@@ -758,8 +773,9 @@ cudaError_t bcr_fill(const IfPtrs& I, int nslab, cudaStream_t s) {
 
 
 cudaError_t if_residual(const IfPtrs& I, const int* row_member, int nrows, int first, cudaStream_t s) {
-    k_if_residual<<<(nrows + 255) / 256, 256, 0, s>>>(I, row_member, nrows, first);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, (void*)&row_member, &nrows, &first};
+    return launch_cluster((const void*)k_if_residual, (nrows + 255) / 256, 256, 0, s, args, 1, true);
 }
 
 cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
@@ -767,7 +783,7 @@ cudaError_t bcr_fwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel};
     const size_t smem = sizeof(float) * (2 * (size_t)nmax + (nmax + SW_CL - 1) / SW_CL);
-    return launch_cluster((const void*)k_bcr_fwd, nel * SW_CL, SW_T, smem, s, args, SW_CL);
+    return launch_cluster((const void*)k_bcr_fwd, nel * SW_CL, SW_T, smem, s, args, SW_CL, true);
 }
 
 cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaStream_t s) {
@@ -775,12 +791,13 @@ cudaError_t bcr_bwd(const IfPtrs& I, const ElimDev* el, int nel, int nmax, cudaS
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel};
     const size_t smem = sizeof(float) * 6 * (size_t)nmax;
-    return launch_cluster((const void*)k_bcr_bwd, nel * SW_CL, SW_T, smem, s, args, SW_CL);
+    return launch_cluster((const void*)k_bcr_bwd, nel * SW_CL, SW_T, smem, s, args, SW_CL, true);
 }
 
 cudaError_t if_update(const IfPtrs& I, int ncols, cudaStream_t s) {
-    k_if_update<<<(ncols + 255) / 256, 256, 0, s>>>(I, ncols);
-    return cudaGetLastError();
+    IfPtrs Ic = I;
+    void* args[] = {&Ic, &ncols};
+    return launch_cluster((const void*)k_if_update, (ncols + 255) / 256, 256, 0, s, args, 1, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -278,6 +278,11 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         mbar_expect_tx(&bar, pbytes);
         bulk_g2s(smem, Pg, pbytes, &bar);
     }
+    // launched as a programmatic dependent of the previous colour: the pack
+    // (written by the basis kernel, two or more launches earlier) is in flight
+    // already; the state is read only once the previous launch is complete
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // Robin data from the current solution, while the pack is in flight:
     // lambda = -beta u.n + pi with n the outward normal of hat-Omega_i and
     // pi = p - u.n h / (2K) of the cell inside
@@ -494,27 +499,37 @@ cudaError_t launch_local2d(const DevPtrs& P, const MethodDev& M, const Job* jobs
     return launch_local_t<float, 32, false>(P, M, jobs, njobs, smem, s);
 }
 
+template <typename T>
+static cudaError_t launch_smooth2d_t(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,
+                                     cudaStream_t s) {
+    auto kern = k_smooth2d<T>;
+    static size_t set_smem = 0;
+    if (smem > set_smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_smem = smem;
+    }
+    // programmatic dependent launch (see k_smooth2d): scheduled while the
+    // previous kernel drains
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nitems);
+    cfg.blockDim = dim3(SM_WARPS * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DevPtrs Pc = P;
+    MethodDev Mc = M;
+    void* args[] = {&Pc, &Mc, (void*)&items};
+    return cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+}
+
 cudaError_t launch_smooth2d(const DevPtrs& P, const MethodDev& M, const int* items, int nitems, size_t smem,
                             cudaStream_t s) {
     if (nitems == 0) return cudaSuccess;
-    if (M.prec == 0) {
-        auto kern = k_smooth2d<double>;
-        static size_t set_smem = 0;
-        if (smem > set_smem) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set_smem = smem;
-        }
-        kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
-    } else {
-        auto kern = k_smooth2d<float>;
-        static size_t set_smem = 0;
-        if (smem > set_smem) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            set_smem = smem;
-        }
-        kern<<<nitems, SM_WARPS * 32, smem, s>>>(P, M, items);
-    }
-    return cudaGetLastError();
+    return M.prec == 0 ? launch_smooth2d_t<double>(P, M, items, nitems, smem, s)
+                       : launch_smooth2d_t<float>(P, M, items, nitems, smem, s);
 }

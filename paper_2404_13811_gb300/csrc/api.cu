@@ -839,7 +839,8 @@ static int read_if_residual(mrcm_handle* h, double* worst) {
         double rn, bn;
         std::memcpy(&rn, &nrm[2 * m], 8);
         std::memcpy(&bn, &nrm[2 * m + 1], 8);
-        w = std::max(w, bn > 0 ? rn / bn : rn);
+        const double r = bn > 0 ? rn / bn : rn;
+        if (!(r <= w)) w = r;   // a NaN residual stays NaN (and is caught as a divergence)
     }
     *worst = w;
     return 0;
@@ -1354,6 +1355,7 @@ static int solve_interface_body(mrcm_handle* h) {
     if (h->slab_variant >= 0 && std::find(cands.begin(), cands.end(), h->slab_variant) == cands.end())
         h->slab_variant = 1;
     if (h->slab_variant < 0 && cands.size() == 1) h->slab_variant = 1;
+    double lu_measured = -1.0;   // the LU's final residual when this call's tuning ran it
     if (h->slab_variant < 0) {
         // autotuner: the cached choice for this shape class, else every
         // admissible slab inverse timed on this solve (device time of the
@@ -1371,18 +1373,30 @@ static int solve_interface_body(mrcm_handle* h) {
             for (int c : cands) {
                 h->slab_variant = c;
                 hist += std::string(" [") + kSlabNames[c] + "]";
-                if ((rc = factor_refine(h, &run[c], &hist))) return rc;
+                if ((rc = factor_refine(h, &run[c], &hist))) {
+                    if (rc != MRCM_ERR_SINGULAR) return rc;
+                    // this variant's refinement diverged: a candidate that lost
+                    run[c].worst = INFINITY;
+                    h->err.clear();
+                    rc = 0;
+                }
                 ok[c] = run[c].worst <= if_target(h);
                 h->tune_ms[c] = run[c].ms;
                 steps[c] = run[c].it;
             }
+            // the fastest that converges; when none does, the one that got
+            // closest (the GMRES fallback continues from its iterate)
             int choice = 1;
             for (int c : cands)
                 if (ok[c] && (!ok[choice] || run[c].ms < run[choice].ms)) choice = c;
+            if (!ok[choice])
+                for (int c : cands)
+                    if (std::isfinite(run[c].worst) && !(run[c].worst >= run[choice].worst)) choice = c;
             h->tune_source = 2;
+            lu_measured = run[1].worst;
             tune_cache_store(key, choice, h->tune_ms, steps);
             h->slab_variant = choice;
-            if (choice == cands.back()) {
+            if (choice == cands.back() && std::isfinite(run[choice].worst)) {
                 o = run[choice];   // the handle's state is the last run's
             } else {
                 hist += std::string(" [") + kSlabNames[choice] + "]";
@@ -1395,10 +1409,12 @@ static int solve_interface_body(mrcm_handle* h) {
     }
     h->if_krylov = false;
     const int max_it = std::max(8, h->prm.max_ir);
-    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it) && h->slab_variant != 1) {
-        // the Gauss-Jordan slab inverses are the less accurate preconditioner on
-        // very ill-conditioned interface systems: refactor with the slab LU and
-        // refine again (the handle keeps the LU for its later solves and captures)
+    if (o.worst > if_target(h) && (o.stalled || o.it >= max_it) && h->slab_variant != 1 &&
+        !(lu_measured >= 0.0 && !(lu_measured < o.worst))) {
+        // a Gauss-Jordan slab inverse may be the less accurate preconditioner on a
+        // very ill-conditioned interface system: refactor with the slab LU and
+        // refine again (the handle keeps the LU for its later solves and
+        // captures), unless this call's tuning measured the LU no closer
         h->slab_variant = 1;
         hist += " (slab LU)";
         if ((rc = factor_refine(h, &o, &hist))) return rc;

@@ -31,9 +31,14 @@
 // multipliers themselves and the pivot row needs no write to a register slot
 // chosen at run time.  The stored rows are divided by c_i at the end.  After
 // the last step the storage holds (P A)^-1 for the row permutation P of the
-// pivots, written out as A^-1 (entry (i, j) to row pinv[i] of column
-// pivrow[j]).  The arithmetic is that of unblocked Gauss-Jordan elimination
-// (n^3 multiply-adds for n unknowns), in FP32.
+// pivots.  The slab eliminated is D^T, and its inverse is written out
+// transposed: D^-1 = ((D^T)^-1)^T, entry (i, j) of the storage going to row
+// pivrow[j] of column pinv[i].  Gauss-Jordan's inverse has the smaller
+// residual on one side; eliminating D^T puts it on the side the reduction
+// uses (the FP64 refinement of the interface solve needs 5 steps on the
+// 512x512 channel workload instead of 9 when D itself is eliminated, the
+// same as with the LU).  The arithmetic is that of unblocked Gauss-Jordan
+// elimination (n^3 multiply-adds for n unknowns), in FP32.
 //
 // Records live in a ring of R slots.  A cluster barrier every G panels
 // bounds how far a producer can run ahead (R = 2 G: a slot is rewritten only
@@ -147,7 +152,8 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
 #pragma unroll
         for (int a = 0; a < RA; ++a) {
             const int i = lane + 32 * a;
-            V[a][b] = (i < np && j < np) ? __ldcg(&A[(size_t)j * np + i]) : (i == j ? 1.f : 0.f);
+            // the transposed slab: entry (i, j) of D^T is A[i np + j] in D's column-major storage
+            V[a][b] = (i < np && j < np) ? __ldcg(&A[(size_t)i * np + j]) : (i == j ? 1.f : 0.f);
         }
     }
     const unsigned rbase = gr_smem(recs), bbase = gr_smem(bars);
@@ -385,12 +391,11 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
         const int j = CW * (int)rank + CB * warp + b;
         const int cj = j < np ? pivrow[j] : np;   // pivots are rows below n <= np; checked all the same
         if (cj < np) {
-            float* dst = Ainv + (size_t)cj * np;
 #pragma unroll
             for (int a = 0; a < RA; ++a) {
                 const int i = lane + 32 * a;
                 const int ri = i < np ? pinv[i] : np;
-                if (ri < np) dst[ri] = V[a][b] * rsc[i];
+                if (ri < np) Ainv[(size_t)ri * np + cj] = V[a][b] * rsc[i];   // (D^T)^-1 transposed
             }
         }
     }

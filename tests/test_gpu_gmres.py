@@ -1,6 +1,6 @@
 """The interface GMRES fallback against the oracle, element by element.
 
-At alpha_basis = 1e4 with overlap the interface system of Eqs.
+At alpha_basis = 1e5 with overlap the interface system of Eqs.
 (int_ujump)-(int_pjump) is too ill-conditioned for stationary refinement
 with the FP32 reduction factor; the solve continues with FP64 GMRES
 preconditioned by that factor (Algorithm 1, Step 5).  The oracle solves the
@@ -23,14 +23,14 @@ def test_interface_gmres_fallback_matches_oracle(overlap):
     from paper_2404_13811_gb300.solver import MRCM
     prob = I.lognormal_problem((128, 128), sigma2=4.0, corr_len=0.1, seed=606)
     prob.f = np.random.default_rng(607).standard_normal(prob.f.shape)
-    s = MRCM(prob, I.Partition((16, 16), overlap), space=1, alpha_basis=1e4, alpha_smooth=1.0, precision="fp64")
+    s = MRCM(prob, I.Partition((16, 16), overlap), space=1, alpha_basis=1e5, alpha_smooth=1.0, precision="fp64")
     s.build_basis()
     s.solve_interface()
     st = L.mrcm_stats(s.h)
     assert st["interface_gmres"], st          # the fallback ran
     p, u = s.fluxes()
     s.close()
-    ref = O.mrcm_os(prob, (16, 16), overlap, 1, 1e4, 1.0, 0)
+    ref = O.mrcm_os(prob, (16, 16), overlap, 1, 1e5, 1.0, 0)
     G, b = ref.G, ref.rhs
     Rr = 1.0 / np.abs(G).max(axis=1)
     Ge = G * Rr[:, None]

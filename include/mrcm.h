@@ -245,7 +245,7 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
  * register-resident Gauss-Jordan: chosen per handle by the autotuner below),
  * ints[6] = 1 when the last interface solve needed the GMRES fallback,
  * ints[7] = where the slab-inverse choice came from (0 not made or not a
- * choice: slabs larger than 512 unknowns always use the LU; 1 the tuning
+ * choice: slabs larger than 768 unknowns always use the LU; 1 the tuning
  * cache; 2 measured on this handle's first interface solve); dbl[0] = last
  * interface relative residual, dbl[1] / dbl[2] / dbl[3] = the measured device
  * ms of variants 0 / 1 / 2 (factorisation + refinement to ir_tol; 0 when not
@@ -254,7 +254,7 @@ int mrcm_backward(mrcm_handle* h, const double* dL_du, const double* dL_dp, doub
  *
  * Autotuner.  The slab inverses of the interface reduction are computed by
  * one of: Gauss-Jordan elimination with the slab held in registers across a
- * cluster of CTAs (one pivot column per step, slabs of at most 512
+ * cluster of CTAs (one pivot column per step, slabs of at most 768
  * unknowns); blocked Gauss-Jordan elimination in shared memory (slabs of at
  * most 256 unknowns); an LU factorisation followed by the inverse columns
  * (any size).  The first mrcm_solve_interface of a handle (and the first

@@ -1346,7 +1346,7 @@ static int solve_interface_body(mrcm_handle* h) {
     RefineOut o;
     int rc = 0;
     // the slab inverses this interface system admits: register-resident
-    // Gauss-Jordan (slabs of up to 512 unknowns), blocked Gauss-Jordan (up to
+    // Gauss-Jordan (slabs of up to 768 unknowns), blocked Gauss-Jordan (up to
     // 256), and the LU (any size)
     std::vector<int> cands;
     if (slab_inverse_gjr_npad(h->npad)) cands.push_back(2);

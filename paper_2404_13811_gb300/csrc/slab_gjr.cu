@@ -115,8 +115,9 @@ struct GrShape {
     static constexpr int RA = NPAD / 32;            // rows per lane
     static constexpr int HDR = 4 * CB;              // record header: (p, pivot, 1 / pivot, 0) per column
     static constexpr int REC = CB * NPAD + HDR;     // floats per record
-    static_assert(RA % 4 == 0 && CB % 4 == 0 && CB * NW * CL == NPAD, "unsupported slab inverse shape");
-    static constexpr int G = NPAD >= 512 ? 4 : 8;   // panels between cluster barriers
+    static_assert(RA % 4 == 0 && (RA < 8 || RA % 8 == 0) && RA <= 32 && CB % 4 == 0 && CB * NW * CL == NPAD,
+                  "unsupported slab inverse shape");
+    static constexpr int G = NPAD >= 768 ? 2 : NPAD >= 512 ? 4 : 8;   // panels between cluster barriers
     static constexpr int R = 2 * G;                  // record slots (one panel each)
     static constexpr size_t smem() { return sizeof(float) * ((size_t)R * REC + (size_t)NW * NPAD * CB); }
 };
@@ -145,15 +146,32 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
     const float* A = I.D + S.offD;
     float* Ainv = I.Dinv + S.offD;
 
+    // the transposed slab: entry (i, j) of D^T is A[i np + j] in D's
+    // column-major storage, so a lane's CB consecutive columns of row i are
+    // contiguous (np and the warp's first column are multiples of 4)
     float V[RA][CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-        const int j = CW * (int)rank + CB * warp + b;
+    {
+        const int j0 = CW * (int)rank + CB * warp;
 #pragma unroll
         for (int a = 0; a < RA; ++a) {
             const int i = lane + 32 * a;
-            // the transposed slab: entry (i, j) of D^T is A[i np + j] in D's column-major storage
-            V[a][b] = (i < np && j < np) ? __ldcg(&A[(size_t)i * np + j]) : (i == j ? 1.f : 0.f);
+#pragma unroll
+            for (int q = 0; q < CB / 4; ++q) {
+                const int j = j0 + 4 * q;
+                float4 t;
+                if (i < np && j < np) {
+                    t = __ldcg(reinterpret_cast<const float4*>(A + (size_t)i * np + j));
+                } else {
+                    t.x = i == j ? 1.f : 0.f;
+                    t.y = i == j + 1 ? 1.f : 0.f;
+                    t.z = i == j + 2 ? 1.f : 0.f;
+                    t.w = i == j + 3 ? 1.f : 0.f;
+                }
+                V[a][4 * q] = t.x;
+                V[a][4 * q + 1] = t.y;
+                V[a][4 * q + 2] = t.z;
+                V[a][4 * q + 3] = t.w;
+            }
         }
     }
     const unsigned rbase = gr_smem(recs), bbase = gr_smem(bars);
@@ -227,28 +245,38 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
                 // 2^-12 relative, the first row among equals (keys carry 2047 - row;
                 // a candidate's key is at least 1024 since NPAD <= 1024), by a tree
                 // over the lane's rows and one warp reduction
-                unsigned kt[RA];
-                float vt[RA];
+                unsigned key = 0u;
+                float best = 0.f;
 #pragma unroll
-                for (int a = 0; a < RA; ++a) {
-                    const float v = fabsf(col[a]);
-                    const unsigned kb = ((v == v ? __float_as_uint(v) : 0u) & ~0x7ffu) | (0x7ffu - (unsigned)(lane + 32 * a));
-                    kt[a] = ((rowok & ~usedm) >> a) & 1u ? kb : 0u;
-                    vt[a] = col[a];
-                }
+                for (int a0 = 0; a0 < RA; a0 += 8) {   // chunks of 8 rows bound the live registers
+                    constexpr int KC = RA < 8 ? RA : 8;
+                    unsigned kt[KC];
+                    float vt[KC];
 #pragma unroll
-                for (int w = 1; w < RA; w <<= 1)
-#pragma unroll
-                    for (int a = 0; a + w < RA; a += 2 * w) {
-                        const bool hi = kt[a + w] > kt[a];
-                        kt[a] = hi ? kt[a + w] : kt[a];
-                        vt[a] = hi ? vt[a + w] : vt[a];
+                    for (int t = 0; t < KC; ++t) {
+                        const int a = a0 + t;
+                        const float v = fabsf(col[a]);
+                        const unsigned kb =
+                            ((v == v ? __float_as_uint(v) : 0u) & ~0x7ffu) | (0x7ffu - (unsigned)(lane + 32 * a));
+                        kt[t] = ((rowok & ~usedm) >> a) & 1u ? kb : 0u;
+                        vt[t] = col[a];
                     }
-                const unsigned key = kt[0];
+#pragma unroll
+                    for (int w = 1; w < KC; w <<= 1)
+#pragma unroll
+                        for (int t = 0; t + w < KC; t += 2 * w) {
+                            const bool hi = kt[t + w] > kt[t];
+                            kt[t] = hi ? kt[t + w] : kt[t];
+                            vt[t] = hi ? vt[t + w] : vt[t];
+                        }
+                    const bool hi = kt[0] > key;
+                    key = hi ? kt[0] : key;
+                    best = hi ? vt[0] : best;
+                }
                 const unsigned km = __reduce_max_sync(GR_FULL, key);
                 const unsigned wl = __ballot_sync(GR_FULL, km != 0u && key == km);
                 const int p = km != 0u ? (int)(0x7ffu - (km & 0x7ffu)) : 0;
-                float piv = __shfl_sync(GR_FULL, vt[0], wl ? __ffs(wl) - 1 : 0);
+                float piv = __shfl_sync(GR_FULL, best, wl ? __ffs(wl) - 1 : 0);
                 if (km == 0u || piv == 0.f) {
                     singular = true;
                     piv = 1e-30f;
@@ -327,7 +355,8 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
                 for (int b = 0; b < CB; ++b) u[c][b] = 0.f;
                 if (k >= n) continue;
                 const float4 ph = *reinterpret_cast<const float4*>(rc + CB * NPAD + 4 * c);
-                const int p = __float_as_int(ph.x) & (NPAD - 1);
+                const int pr = __float_as_int(ph.x);
+                const int p = (unsigned)pr < (unsigned)NPAD ? pr : 0;   // a record from a run that timed out may hold anything
                 const float ip = ph.z;
                 float x[CB];
 #pragma unroll
@@ -413,6 +442,8 @@ cudaError_t launch_gjr(const IfPtrs& I, const ElimDev* el, int nel, int* status,
     if (smem > set_smem) {
         cudaError_t e =
             cudaFuncSetAttribute(k_gjr_inverse<NPAD, CL, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && CL > 8)
+            e = cudaFuncSetAttribute(k_gjr_inverse<NPAD, CL, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }
@@ -436,8 +467,10 @@ cudaError_t launch_gjr(const IfPtrs& I, const ElimDev* el, int nel, int* status,
 }  // namespace
 
 // Template slab size of the register-resident Gauss-Jordan inverse for a
-// padded slab size, 0 when it has none (slabs above 512 unknowns).
-int slab_inverse_gjr_npad(int npad) { return npad <= 128 ? 128 : npad <= 256 ? 256 : npad <= 512 ? 512 : 0; }
+// padded slab size, 0 when it has none (slabs above 768 unknowns).
+int slab_inverse_gjr_npad(int npad) {
+    return npad <= 128 ? 128 : npad <= 256 ? 256 : npad <= 512 ? 512 : npad <= 768 ? 768 : 0;
+}
 
 // One elimination level's slab inverses: the larger cluster when all the
 // level's clusters fit on the GPU at once (one CTA per SM), else the smaller.
@@ -447,13 +480,19 @@ cudaError_t gjr_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // latency-bound levels (few slabs): 8 CTAs of 8 warps per slab; large
-    // batches: fewer, wider CTAs per slab (less cluster traffic per column)
-    const bool few = nel * 8 <= nsm;
+    // latency-bound levels (few slabs): 16 CTAs of 4 warps or 8 CTAs of 8
+    // warps per slab when the level's clusters all fit at once (less work and
+    // contention per SM on the chain); large batches: fewer, wider CTAs per
+    // slab (less cluster traffic per column)
+    const bool very_few = nel * 16 <= nsm, few = nel * 8 <= nsm;
     switch (slab_inverse_gjr_npad(I.npad)) {
         case 128: return few ? launch_gjr<128, 4, 8>(I, el, nel, status, s) : launch_gjr<128, 2, 16>(I, el, nel, status, s);
-        case 256: return few ? launch_gjr<256, 8, 8>(I, el, nel, status, s) : launch_gjr<256, 4, 16>(I, el, nel, status, s);
-        case 512: return launch_gjr<512, 8, 16>(I, el, nel, status, s);
+        case 256:
+            return very_few ? launch_gjr<256, 16, 4>(I, el, nel, status, s)
+                 : few      ? launch_gjr<256, 8, 8>(I, el, nel, status, s)
+                            : launch_gjr<256, 4, 16>(I, el, nel, status, s);
+        case 512: return very_few ? launch_gjr<512, 16, 8>(I, el, nel, status, s) : launch_gjr<512, 8, 16>(I, el, nel, status, s);
+        case 768: return launch_gjr<768, 16, 12>(I, el, nel, status, s);   // 16 CTAs of 12 warps
         default: return cudaErrorInvalidValue;
     }
 }

@@ -3,7 +3,7 @@ layers of subdomains, Algorithm 1 Step 5) against the CPU oracle: the choice
 is forced through the tuning cache, and each variant must give the mixed form
 within its bar (relative L2 of fluxes and pressures <= 1e-8) with the slab
 sizes of each template of the register-resident Gauss-Jordan inverse (padded
-slabs of 128, 256 and 512 unknowns) and of the blocked and LU inverses."""
+slabs of 128, 256, 512 and 768 unknowns) and of the blocked and LU inverses."""
 import json
 
 import numpy as np
@@ -36,6 +36,7 @@ CASES = {
     "384x128_P1": ((384, 128), 1),     # at most 188 -> 256 template
     "1024x64_P0": ((1024, 64), 0),     # at most 254 -> 256 template
     "1024x64_P1": ((1024, 64), 1),     # at most 508 -> 512 template (8-CTA clusters)
+    "1536x64_P1": ((1536, 64), 1),     # at most 764 -> 768 template (16-CTA clusters)
 }
 
 

@@ -293,17 +293,21 @@ __device__ void apply_coupling(const float* AT, int M, int M2, const float* Cg, 
 
 // ---------------------------------------------------------------------------
 // One block-cyclic-reduction elimination of slab j (after Dinv_j is known),
-// one cluster of 4 CTAs.  With Qv / Qm the columns of Dinv_j at j's
-// pressure / flux coupling rows, Rup = Cup_jm and Rdn = Cdn_jp (saved first):
-//   rank 0: D_jm[mrows] -= (Rup Qv) Cdn_j      rank 1: Cup_jm <- -(Rup Qm) Cup_j
-//   rank 2: D_jp[vrows] -= (Rdn Qm) Cup_j      rank 3: Cdn_jp <- -(Rdn Qv) Cdn_j
+// one cluster of 4, 8 or 16 CTAs.  With Qv / Qm the columns of Dinv_j at j's
+// pressure / flux coupling rows, Rup = Cup_jm and Rdn = Cdn_jp (saved first),
+// CTA r computes product r mod 4 on the (r / 4)-th chunk of its rows:
+//   0: D_jm[mrows] -= (Rup Qv) Cdn_j      1: Cup_jm <- -(Rup Qm) Cup_j
+//   2: D_jp[vrows] -= (Rdn Qm) Cup_j      3: Cdn_jp <- -(Rdn Qv) Cdn_j
+// (every target row is written by one CTA only).
 // ---------------------------------------------------------------------------
 constexpr int EL_THREADS = 512;
 
 __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev* el, int nel) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int e = blockIdx.x / GJ_CL;
+    const int CL = (int)cluster.num_blocks();
+    const int e = blockIdx.x / CL;
+    const int prod = rank & 3, chunk = rank >> 2, nch = CL >> 2;
     extern __shared__ __align__(16) float esm[];
     const bool active = e < nel;
     ElimDev E{0, 0, -1};
@@ -321,13 +325,13 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
     if (active) {
         // save the couplings into j (split over the cluster)
         const float* CupM = I.Cup + Sm.offCup;
-        for (int t = tid + rank * nt; t < Sm.nm * Sj.n; t += nt * GJ_CL) {
+        for (int t = tid + rank * nt; t < Sm.nm * Sj.n; t += nt * CL) {
             const int r = t / Sj.n, c = t - (t / Sj.n) * Sj.n;
             Rup[t] = CupM[(size_t)r * Sm.ldc + c];
         }
         if (E.jp >= 0) {
             const float* CdnP = I.Cdn + Sp.offCdn;
-            for (int t = tid + rank * nt; t < Sp.nv * Sj.n; t += nt * GJ_CL) {
+            for (int t = tid + rank * nt; t < Sp.nv * Sj.n; t += nt * CL) {
                 const int r = t / Sj.n, c = t - (t / Sj.n) * Sj.n;
                 Rdn[t] = CdnP[(size_t)r * Sp.ldc + c];
             }
@@ -341,19 +345,25 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
     const int* vrows_j = mrows_j + Sj.nm;
     const float* Cdn_j = I.Cdn + Sj.offCdn;  // nv_j x ldc, columns = jm unknowns
     const float* Cup_j = I.Cup + Sj.offCup;  // nm_j x ldc, columns = jp unknowns
-    const bool up = rank < 2;
+    const bool up = prod < 2;
     if (!up && E.jp < 0) return;
-    const float* Lrows = up ? Rup : Rdn;
-    const int M = up ? Sm.nm : Sp.nv;
-    const bool useQv = (rank == 0 || rank == 3);
+    const bool useQv = (prod == 0 || prod == 3);
     const int N = useQv ? Sj.nv : Sj.nm;
     const int* cols = useQv ? vrows_j : mrows_j;
-    if (rank == 1 && E.jp < 0) {
+    if (prod == 1 && E.jp < 0) {
         // no slab above any more: jm loses its upper coupling
         float* CupM = I.Cup + Sm.offCup;
-        for (int t = tid; t < Sm.nm * Sm.ldc; t += nt) CupM[t] = 0.f;
+        if (chunk == 0)
+            for (int t = tid; t < Sm.nm * Sm.ldc; t += nt) CupM[t] = 0.f;
         return;
     }
+    // this CTA's rows [r0, r0 + M) of the product's M_all rows
+    const int Mall = up ? Sm.nm : Sp.nv;
+    const int mw = (Mall + nch - 1) / nch;
+    const int r0 = min(Mall, chunk * mw);
+    const int M = min(Mall, r0 + mw) - r0;
+    if (M <= 0) return;
+    const float* Lrows = (up ? Rup : Rdn) + (size_t)r0 * Sj.n;
     const int Mp = (M + 3) & ~3, Np = (N + 3) & ~3;
     float* Asm = esm;                   // (L Q)^T, Np x Mp
     float* stL = Asm + Np * Mp;         // 32 x (Mp + 4)
@@ -361,18 +371,18 @@ __global__ void __launch_bounds__(EL_THREADS) k_bcr_elim(IfPtrs I, const ElimDev
     float* Csm = stQ + 32 * (Np + 4);   // Np x (column chunk rounded up to 4)
     __syncthreads();
     rows_times_cols(Lrows, M, Sj.n, Dinv, np, cols, N, Asm, stL, stQ);
-    if (rank == 0) {
-        apply_coupling<true>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, I.D + Sm.offD, np, I.idx + Sm.offIdx,
-                             nullptr, 0, 0);
-    } else if (rank == 1) {
-        apply_coupling<false>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.elim_cw, nullptr, np, nullptr, I.Cup + Sm.offCup,
-                              Sm.ldc, Sm.ldc);
-    } else if (rank == 2) {
+    if (prod == 0) {
+        apply_coupling<true>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, I.D + Sm.offD, np,
+                             I.idx + Sm.offIdx + r0, nullptr, 0, 0);
+    } else if (prod == 1) {
+        apply_coupling<false>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.elim_cw, nullptr, np, nullptr,
+                              I.Cup + Sm.offCup + (size_t)r0 * Sm.ldc, Sm.ldc, Sm.ldc);
+    } else if (prod == 2) {
         apply_coupling<true>(Asm, M, N, Cup_j, Sj.ldc, Sp.n, Csm, I.elim_cw, I.D + Sp.offD, np,
-                             I.idx + Sp.offIdx + Sp.nm, nullptr, 0, 0);
+                             I.idx + Sp.offIdx + Sp.nm + r0, nullptr, 0, 0);
     } else {
-        apply_coupling<false>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, nullptr, np, nullptr, I.Cdn + Sp.offCdn,
-                              Sp.ldc, Sp.ldc);
+        apply_coupling<false>(Asm, M, N, Cdn_j, Sj.ldc, Sm.n, Csm, I.elim_cw, nullptr, np, nullptr,
+                              I.Cdn + Sp.offCdn + (size_t)r0 * Sp.ldc, Sp.ldc, Sp.ldc);
     }
 }
 
@@ -1571,10 +1581,18 @@ cudaError_t bcr_elim(const IfPtrs& I, const ElimDev* el, int nel, size_t smem, c
     static size_t set_smem = 0;
     if (smem > set_smem) {
         cudaError_t e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bcr_elim, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         set_smem = smem;
     }
+    // the upper levels eliminate few slabs: more CTAs per slab (row chunks of
+    // the four products) while the level's clusters fit on the GPU at once
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int cl = nel * 16 <= nsm ? 16 : nel * 8 <= nsm ? 8 : GJ_CL;
     IfPtrs Ic = I;
     void* args[] = {&Ic, (void*)&el, &nel};
-    return launch_cluster((const void*)k_bcr_elim, nel * GJ_CL, EL_THREADS, smem, s, args);
+    return launch_cluster((const void*)k_bcr_elim, nel * cl, EL_THREADS, smem, s, args, cl);
 }

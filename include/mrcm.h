@@ -47,6 +47,11 @@ extern "C" {
 #define MRCM_ERR_NOMEM (-8)          /* device allocation failed */
 #define MRCM_ERR_TIMEOUT (-9)        /* a kernel's bounded wait (for a staged copy) ran out; the kernel
                                         returned without its result (the context stays usable) */
+#define MRCM_ERR_CHECK (-10)         /* bounds-check build only (libmrcm_check.so, compiled with
+                                        -DMRCM_CHECK=1): a kernel's check of a shared-memory layout,
+                                        a bulk copy, a pivot record or a write index failed; the
+                                        guarded access was skipped; mrcm_last_error names the site,
+                                        the block and the value */
 
 #define MRCM_NEUMANN 0   /* u.n = value on the side (Eq. (1d)) */
 #define MRCM_DIRICHLET 1 /* p = value on the side (Eq. (1c)) */

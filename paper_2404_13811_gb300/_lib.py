@@ -11,6 +11,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libmrcm.so")
+LIBPATH_CHECK = os.path.join(HERE, "libmrcm_check.so")   # the bounds-check build (MRCM_CHECK=1)
 
 MRCM_OK = 0
 MRCM_NEUMANN, MRCM_DIRICHLET = 0, 1
@@ -19,7 +20,7 @@ MRCM_FP64, MRCM_MIXED = 0, 1
 ERRORS = {
     -1: "MRCM_ERR_BAD_INPUT", -2: "MRCM_ERR_STATE", -3: "MRCM_ERR_CUDA", -4: "MRCM_ERR_NOT_SPD",
     -5: "MRCM_ERR_NO_CONVERGENCE", -6: "MRCM_ERR_SINGULAR", -7: "MRCM_ERR_UNSUPPORTED",
-    -8: "MRCM_ERR_NOMEM", -9: "MRCM_ERR_TIMEOUT",
+    -8: "MRCM_ERR_NOMEM", -9: "MRCM_ERR_TIMEOUT", -10: "MRCM_ERR_CHECK",
 }
 
 
@@ -56,11 +57,15 @@ class MrcmError(RuntimeError):
         self.code = code
 
 
-def load(path=LIBPATH):
-    """Loads the library (raises OSError if it was not built)."""
+def load(path=None):
+    """Loads the library (raises OSError if it was not built): libmrcm.so, or
+    the bounds-check build libmrcm_check.so when the environment has
+    MRCM_CHECK=1."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIBPATH_CHECK if os.environ.get("MRCM_CHECK") == "1" else LIBPATH
     if not os.path.exists(path):
         raise OSError(f"{path} not found: build it with paper_2404_13811_gb300.build.build()")
     lib = C.CDLL(path)

@@ -542,7 +542,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     if ((e = dalloc(h, &h->d_pbar, (size_t)nitems * h->ncell_i_max))) return e;
     if ((e = dalloc(h, &h->d_ubg, (size_t)nitems * MRCM_MAXSIDE * h->side_max))) return e;
     if ((e = dalloc(h, &h->d_mom, (size_t)nitems * (h->nbasis_max + 1) * MRCM_MAXSIDE * h->npsi * 2))) return e;
-    if ((e = dalloc(h, &h->d_status, 4))) return e;
+    if ((e = dalloc(h, &h->d_status, MRCM_STATUS_WORDS))) return e;
     if ((e = dalloc(h, &h->d_mean, nmem))) return e;
     cudaStream_t st = h->stream;
     CUDA_TRY(h, cudaMemcpyAsync(h->d_mem, h->mem.data(), sizeof(MemberDev) * nmem, cudaMemcpyHostToDevice, st));
@@ -562,7 +562,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         for (auto& md : h->mem) maxc = std::max(maxc, (long long)md.n[0] * md.n[1] * md.n[2]);
         CUDA_TRY(h, launch_faces(h->d_mem, nmem, maxc, h->d_K, h->d_Tf, h->d_hk, h->d_wh, st));
     }
-    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * MRCM_STATUS_WORDS, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->ncells, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_u, 0, sizeof(double) * h->ncells * 2 * d, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_mom, 0,
@@ -681,6 +681,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     IfPtrs& I = h->I;
     const int NB = h->nbasis_max;
     I.NB = NB;
+    I.status = h->d_status;
     I.npad = npad;
     I.xch = xch;
     I.elim_cw = elim_cw;
@@ -718,13 +719,18 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
 }
 
 static int check_status(mrcm_handle* h) {
-    int st[4];
-    CUDA_TRY(h, cudaMemcpyAsync(st, h->d_status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    int st[MRCM_STATUS_WORDS];
+    CUDA_TRY(h, cudaMemcpyAsync(st, h->d_status, sizeof(int) * MRCM_STATUS_WORDS, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->loc_ir = std::max(h->loc_ir, st[1]);
     if (st[0] & ST_NOT_SPD) return fail(h, MRCM_ERR_NOT_SPD, "non-positive pivot in a local factorisation (item " + std::to_string(st[2]) + ")");
     if (st[0] & ST_NO_CONV) return fail(h, MRCM_ERR_NO_CONVERGENCE, "local iterative refinement did not reach ir_tol");
     if (st[0] & ST_BAD) return fail(h, MRCM_ERR_TIMEOUT, "a staged copy did not complete within its wait limit");
+    if (st[0] & ST_CHECK) {
+        const long long v = (long long)(unsigned)st[6] | ((long long)st[7] << 32);
+        return fail(h, MRCM_ERR_CHECK, "bounds check failed at site " + std::to_string(st[4]) + " (block " +
+                                           std::to_string(st[5]) + ", value " + std::to_string(v) + ")");
+    }
     return 0;
 }
 
@@ -1603,7 +1609,7 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
         CUDA_TRY(h, cudaMemcpyAsync(tmp, values, sizeof(double) * nc, cudaMemcpyHostToDevice, st));
         src = tmp;
     }
-    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * MRCM_STATUS_WORDS, st));
     CUDA_TRY(h, launch_set_K(src, h->d_K, nc, is_log, h->d_status, st));
     if (tmp) CUDA_TRY(h, cudaFreeAsync(tmp, st));
     long long maxc = 0;
@@ -1654,7 +1660,7 @@ static int adjoint_body(mrcm_handle* h, const double* gp, const double* gu, doub
         W.snap_len = need;
     }
     const int nitems = (int)h->sub.size();
-    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * MRCM_STATUS_WORDS, st));
     // replay: the MRCM-O state again, then the smoothing steps, recording the
     // state before every colour pass (forward solves with the kept factors)
     if ((rc = issue_assemble(h))) return rc;

@@ -1101,6 +1101,7 @@ struct Carve {
     double* X; // nrhs * n
     T* W;      // nrhs * n
     int* flags;
+    size_t end;   // bytes of shared memory the layout takes
 };
 
 template <typename T>
@@ -1141,6 +1142,7 @@ __device__ Carve<T> carve(unsigned char* base, int nx, int ny, int nrhs, bool pa
     if (std::is_same<T, double>::value) C.X = (double*)C.W;
     C.cxs = C.W;   // the in-line couplings are needed only while factoring, before any solve
     C.flags = (int*)take(64);
+    C.end = o;
     return C;
 }
 

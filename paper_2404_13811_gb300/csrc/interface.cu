@@ -154,11 +154,14 @@ __global__ void k_bcr_fill(IfPtrs I, int nslab) {
                 const int c = c0 + k;
                 const float v = (float)(Rr * gv[b * I.NB + k] * I.Cs[c]);
                 if (c >= S.col0 && c < S.col0 + S.n) {
-                    D[(size_t)(c - S.col0) * np + rr] = v;
+                    if (mrcm_check(I.status, rr < np && c - S.col0 < np, 8, c)) D[(size_t)(c - S.col0) * np + rr] = v;
                 } else if (S.up >= 0 && c >= colU && c < colU + I.slabs[S.up].n) {
-                    Cup[(size_t)mpos[rr] * S.ldc + (c - colU)] = v;
+                    if (mrcm_check(I.status, mpos[rr] >= 0 && mpos[rr] < S.nm && c - colU < S.ldc, 8, mpos[rr]))
+                        Cup[(size_t)mpos[rr] * S.ldc + (c - colU)] = v;
                 } else if (S.dn >= 0) {
-                    Cdn[(size_t)vpos[rr] * S.ldc + (c - colD)] = v;
+                    if (mrcm_check(I.status, vpos[rr] >= 0 && vpos[rr] < S.nv && c - colD >= 0 && c - colD < S.ldc, 8,
+                                   vpos[rr]))
+                        Cdn[(size_t)vpos[rr] * S.ldc + (c - colD)] = v;
                 }
             }
         }

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
     __syncthreads();
     const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (job.type == JOB_PART ? 1 : 0);
     Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? min(nrhs, NWARP) : 1, job.type == JOB_PART);
+    if (!mrcm_check(P.status, C.end <= mrcm_dyn_smem_bytes(), 1, (long long)C.end)) return;   // uniform
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
     build_ops(B, md, P, C.O);
     fill_scale(B, C.O, mixed);
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
     double* x = (double*)take(sizeof(double) * n);
     T* w = mixed ? (T*)take(sizeof(T) * n) : (T*)x;
     int* flags = (int*)take(64);
+    if (!mrcm_check(P.status, o <= mrcm_dyn_smem_bytes(), 2, (long long)o)) return;   // uniform
     const uint32_t pbytes = (uint32_t)L.bytes;
     const unsigned char* Pg = (const unsigned char*)((const T*)P.fac + (size_t)item * P.fac_stride);
     if (threadIdx.x == 0) {
@@ -276,7 +278,10 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         mbar_init(&bar, 1);
         if (Mth.wait0 > 0) mbar_init(&never, 1);
         mbar_expect_tx(&bar, pbytes);
-        bulk_g2s(smem, Pg, pbytes, &bar);
+        // a bulk copy needs 16-byte aligned ends and a size that is a multiple of 16
+        if (mrcm_check(P.status, ((uintptr_t)Pg & 15) == 0 && (pbytes & 15) == 0 && pbytes <= L.bytes, 3,
+                       (long long)pbytes))
+            bulk_g2s(smem, Pg, pbytes, &bar);
     }
     // launched as a programmatic dependent of the previous colour: the pack
     // (written by the basis kernel, two or more launches earlier) is in flight
@@ -386,6 +391,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32) k_smooth2d(DevPtrs P, MethodDev
         const int i = c % nIx + offx, j = c / nIx + offy;
         const int cl = j * B.nx + i;
         const long long g = (B.lo[0] + i) + (long long)md.n[0] * (B.lo[1] + j);
+        if (!mrcm_check(P.status, g >= 0 && g < (long long)md.n[0] * md.n[1], 4, g)) continue;
         const double pc = x[cl];
         pw[g] = pc;
         // transmissibilities: prefetched for a thread's first two cells, else read here

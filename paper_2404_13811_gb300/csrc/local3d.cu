@@ -616,6 +616,7 @@ struct Carve3 {
     double* macc;
     int* flags;
     unsigned int* nrm;
+    size_t end;   // bytes of shared memory the layout takes
 };
 
 template <typename T>
@@ -672,6 +673,7 @@ __device__ Carve3<T> carve3(unsigned char* base, const Box3& B, bool stored_rhs,
     C.flags = (int*)take(32);
     C.nrm = (unsigned int*)take(64);
     C.bar = (uint64_t*)take(16);
+    C.end = o;
     return C;
 }
 
@@ -698,6 +700,7 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
     __syncthreads();
     const bool part = job.type == JOB_PART;
     Carve3<T> C = carve3<T>(smem, B, part, P.xs + (size_t)blockIdx.x * P.xs_stride);
+    if (!mrcm_check(P.status, C.end <= mrcm_dyn_smem_bytes(), 6, (long long)C.end)) return;   // uniform
     uint32_t par[2] = {0u, 0u};
     if (threadIdx.x == 0) {
         C.flags[0] = 0;
@@ -869,6 +872,7 @@ __global__ void __launch_bounds__(T3) k_smooth3d(DevPtrs P, MethodDev Mth, const
     }
     __syncthreads();
     Carve3<T> C = carve3<T>(smem, B, true, P.xs + (size_t)blockIdx.x * P.xs_stride);
+    if (!mrcm_check(P.status, C.end <= mrcm_dyn_smem_bytes(), 6, (long long)C.end)) return;   // uniform
     uint32_t par[2] = {0u, 0u};
     if (threadIdx.x == 0) {
         C.flags[0] = 0;
@@ -931,6 +935,7 @@ __global__ void __launch_bounds__(T3) k_smooth3d(DevPtrs P, MethodDev Mth, const
         c[2] = ci / (nI[0] * nI[1]) + off[2];
         const int t = bidx(B, c);
         const long long g = gidx(B, md, c);
+        if (!mrcm_check(P.status, g >= 0 && g < (long long)md.n[0] * md.n[1] * md.n[2], 7, g)) continue;
         const double pc = x[t];
         pw[g] = pc;
         for (int sid = 0; sid < 6; ++sid) {
@@ -993,6 +998,7 @@ __global__ void k_assemble3d(DevPtrs P, const double* __restrict__ X) {
         c[1] = (ci / nI[0]) % nI[1];
         c[2] = ci / (nI[0] * nI[1]);
         const long long g = (sd.lo[0] + c[0]) + (long long)md.n[0] * ((sd.lo[1] + c[1]) + (long long)md.n[1] * (sd.lo[2] + c[2]));
+        if (!mrcm_check(P.status, g >= 0 && g < (long long)md.n[0] * md.n[1] * md.n[2], 7, g)) continue;
         const double pc = ps3[ci];
         pw[g] = pc;
         for (int sid = 0; sid < 6; ++sid) {

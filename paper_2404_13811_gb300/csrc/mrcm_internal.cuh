@@ -93,7 +93,8 @@ struct DevPtrs {
     double* ubg;         // [item][2d][side_max]
     double* mom;         // [item][nbasis_max+1][2d][npsi][2]  (flux, pressure moments)
     int nbasis_max, ncell_i_max, side_max, npsi;
-    int* status;         // [0] error bits, [1] max local refinement steps, [2] bad item
+    int* status;         // [0] error bits, [1] max local refinement steps, [2] bad item, [3] refinement
+                         // steps, [4..7] the first failed check of the bounds-check build
 };
 
 struct MethodDev {
@@ -127,6 +128,7 @@ struct IfPtrs {
     int* idx;      // row index lists per slab
     const SlabDev* slabs;
     unsigned long long* rnorm;   // [2 * nmember]: residual max, rhs max (bit patterns)
+    int* status;   // the handle's status words (bounds-check build)
     int NB;
     int npad;
     int xch;       // inverse columns solved together by the slab LU (fits shared memory)
@@ -151,11 +153,54 @@ struct AdjPtrs {
     const double* X;     // forward interface solution
 };
 
+// Bounds-check build (compiled with -DMRCM_CHECK=1 into libmrcm_check.so):
+// kernels test their shared-memory layouts against the launch's dynamic
+// shared memory, the addresses and sizes of their bulk copies, the pivot
+// records of the slab inverses and the cell indices of their state and
+// slab-block writes; the first failed check is recorded in status[4..7]
+// (site, block, value low / high word), the access it guards is skipped and
+// the call returns MRCM_ERR_CHECK.  Without the flag every check is the
+// constant true.  Sites: 1 k_local2d layout, 2 k_smooth2d layout, 3 its pack
+// copy, 4 its state writes, 5 k_assemble2d state writes, 6 k_local3d /
+// k_smooth3d layout, 7 k_smooth3d / k_assemble3d-style 3D state writes,
+// 8 k_bcr_fill block writes, 9 k_gjr_inverse pivot records, 10 its inverse
+// writes.
+#ifndef MRCM_CHECK
+#define MRCM_CHECK 0
+#endif
+#define MRCM_STATUS_WORDS 8
+
+__device__ __forceinline__ bool mrcm_check(int* status, bool ok, int site, long long value) {
+#if MRCM_CHECK
+    if (!ok && status) {
+        if (atomicCAS(&status[4], 0, site) == 0) {
+            status[5] = (int)blockIdx.x;
+            status[6] = (int)(value & 0xffffffffLL);
+            status[7] = (int)(value >> 32);
+        }
+        atomicOr(&status[0], 32);
+    }
+    return ok;
+#else
+    (void)status;
+    (void)site;
+    (void)value;
+    return true;
+#endif
+}
+
+__device__ __forceinline__ unsigned mrcm_dyn_smem_bytes() {
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 // status bits
 #define ST_NOT_SPD 1
 #define ST_NO_CONV 2
 #define ST_SINGULAR 4
 #define ST_BAD 8         // a staged (bulk) copy did not arrive within its wait limit
 #define ST_BAD_K 16      // a permeability that is not positive and finite
+#define ST_CHECK 32      // a check of the bounds-check build failed (status[4..7])
 
 static inline __host__ __device__ int side_axis(int sid) { return sid >> 1; }

@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
                 if (k >= n) continue;
                 const float4 ph = *reinterpret_cast<const float4*>(rc + CB * NPAD + 4 * c);
                 const int pr = __float_as_int(ph.x);
-                const int p = (unsigned)pr < (unsigned)NPAD ? pr : 0;   // a record from a run that timed out may hold anything
+                const int p = mrcm_check(status, timed_out || (unsigned)pr < (unsigned)n, 9, pr) && (unsigned)pr < (unsigned)NPAD
+                                  ? pr
+                                  : 0;   // a record from a run that timed out may hold anything
                 const float ip = ph.z;
                 float x[CB];
 #pragma unroll
@@ -424,7 +426,8 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
             for (int a = 0; a < RA; ++a) {
                 const int i = lane + 32 * a;
                 const int ri = i < np ? pinv[i] : np;
-                if (ri < np) Ainv[(size_t)ri * np + cj] = V[a][b] * rsc[i];   // (D^T)^-1 transposed
+                if (mrcm_check(status, ri < np || i >= np, 10, ri) && ri < np)
+                    Ainv[(size_t)ri * np + cj] = V[a][b] * rsc[i];   // (D^T)^-1 transposed
             }
         }
     }

@@ -33,6 +33,7 @@ __global__ void k_assemble2d(DevPtrs P, const double* __restrict__ X) {
         const int i = c % nIx, j = c / nIx;
         const int gx = sd.lo[0] + i, gy = sd.lo[1] + j;
         const long long g = gx + (long long)md.n[0] * gy;
+        if (!mrcm_check(P.status, g >= 0 && g < (long long)md.n[0] * md.n[1], 5, g)) continue;
         const double pc = ps[c];
         const double kc = K[g];
         pw[g] = pc;

@@ -98,6 +98,16 @@ __device__ __forceinline__ float gr_rcp(float x) {
     return fmaf(r, e, r);
 }
 
+__device__ __forceinline__ void gr_release(int* flag, int v) {
+    asm volatile("st.release.cta.shared::cta.s32 [%0], %1;" ::"r"(gr_smem(flag)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int gr_acquire(const int* flag) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(gr_smem(flag)) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void gr_cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -131,6 +141,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
     float* recs = gr_dyn;                  // [R][REC]
     float* tiles = recs + R * REC;         // [warp][NPAD][CB]
     __shared__ __align__(8) unsigned long long bars[R];
+    __shared__ int colready[R];            // columns of a slot's record written so far (P CB + c + 1)
     __shared__ int pivrow[NPAD];           // pivot row of every step
     __shared__ float pivval[NPAD];         // its pivot
     __shared__ int pinv[NPAD];             // step at which each row was the pivot
@@ -188,6 +199,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
         pivrow[i] = i;
         pivval[i] = 1.f;
     }
+    if (tid < R) colready[tid] = 0;
     gr_cluster_sync();
 
     unsigned usedm = 0u;   // bit a: row lane + 32 a has been a pivot
@@ -209,7 +221,11 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
         const unsigned bar = bbase + 8u * (unsigned)slot;
         float* rc = recs + slot * REC;
         const bool mine = P / NW == (int)rank && P % NW == warp;
-        if (!mine && !timed_out) {
+        // the owner of the next panel, when both panels are this CTA's, takes
+        // the record column by column as it is written (its update of the
+        // last column is then all that stands between the two panels)
+        const bool follow = !mine && P / NW == (int)rank && (P + 1) / NW == (int)rank && (P + 1) % NW == warp;
+        if (!mine && !follow && !timed_out) {
             long long it = 0;
             while (!gr_try(bar, (unsigned)(P / R) & 1u))
                 if (++it > GR_WAIT_LIMIT) {
@@ -296,6 +312,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
                     pivval[k] = piv;
                 }
                 __syncwarp();
+                if (lane == 0) gr_release(&colready[slot], P * CB + c + 1);   // column c of the record is complete
                 // row p on the other columns just before this step, from the panel's
                 // start and the multipliers recorded so far: columns not yet pivots
                 // start from the copy, pivot columns b < c from their fixed values
@@ -354,6 +371,14 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
 #pragma unroll
                 for (int b = 0; b < CB; ++b) u[c][b] = 0.f;
                 if (k >= n) continue;
+                if (follow && !timed_out) {
+                    long long it = 0;
+                    while (gr_acquire(&colready[slot]) < k + 1)
+                        if (++it > GR_WAIT_LIMIT) {
+                            timed_out = true;
+                            break;
+                        }
+                }
                 const float4 ph = *reinterpret_cast<const float4*>(rc + CB * NPAD + 4 * c);
                 const int pr = __float_as_int(ph.x);
                 const int p = mrcm_check(status, timed_out || (unsigned)pr < (unsigned)n, 9, pr) && (unsigned)pr < (unsigned)NPAD
@@ -382,9 +407,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_gjr_inverse(IfPtrs I, const Elim
                     pivrow[k] = p;
                     pivval[k] = ph.y;
                 }
-            }
-#pragma unroll
-            for (int c = 0; c < CB; ++c) {
+                // the column's rank-1 update (the order over the panel's columns per entry is kept)
                 float m[RA];
 #pragma unroll
                 for (int q = 0; q < RA / 4; ++q) {
@@ -483,17 +506,13 @@ cudaError_t gjr_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    // latency-bound levels (few slabs): 16 CTAs of 4 warps or 8 CTAs of 8
-    // warps per slab when the level's clusters all fit at once (less work and
-    // contention per SM on the chain); large batches: fewer, wider CTAs per
-    // slab (less cluster traffic per column)
+    // latency-bound levels (few slabs): 8 CTAs of 8 warps per slab (16 of 8
+    // for 512 unknowns) when the level's clusters all fit at once; large
+    // batches: fewer, wider CTAs per slab (less cluster traffic per column)
     const bool very_few = nel * 16 <= nsm, few = nel * 8 <= nsm;
     switch (slab_inverse_gjr_npad(I.npad)) {
         case 128: return few ? launch_gjr<128, 4, 8>(I, el, nel, status, s) : launch_gjr<128, 2, 16>(I, el, nel, status, s);
-        case 256:
-            return very_few ? launch_gjr<256, 16, 4>(I, el, nel, status, s)
-                 : few      ? launch_gjr<256, 8, 8>(I, el, nel, status, s)
-                            : launch_gjr<256, 4, 16>(I, el, nel, status, s);
+        case 256: return few ? launch_gjr<256, 8, 8>(I, el, nel, status, s) : launch_gjr<256, 4, 16>(I, el, nel, status, s);
         case 512: return very_few ? launch_gjr<512, 16, 8>(I, el, nel, status, s) : launch_gjr<512, 8, 16>(I, el, nel, status, s);
         case 768: return launch_gjr<768, 16, 12>(I, el, nel, status, s);   // 16 CTAs of 12 warps
         default: return cudaErrorInvalidValue;

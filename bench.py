@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle check and CPU baseline")
+    ap.add_argument("--space", type=int, default=None, choices=[0, 1],
+                    help="layered3d only: interface spaces, 0 = P0 (the default workload), 1 = P1 = {1, s, t} "
+                         "(up to 18 basis right-hand sides per box)")
     ap.add_argument("--grid", default=None,
                     help="layered3d only: cells per axis as nx,ny,nz (default 60,220,85; the layer split "
                          "keeps its share of the z extent)")
@@ -492,10 +495,12 @@ def run_other(args):
     line = {"workload": w, "unit": "cells/s", "steps": args.steps, "warmup": args.warmup,
             "l2": "flushed (512 MB write) between timed steps", "data": "synthetic", "peaks": peaks}
     if w in ("small", "layered3d", "ensemble"):
-        if w == "layered3d" and args.grid:
-            n3 = tuple(int(v) for v in args.grid.split(","))
-            cases = [I.config_layered3d(n=n3, n_upper=max(1, round(35 * n3[2] / 85)))]
+        if w == "layered3d" and (args.grid or args.space is not None):
+            n3 = tuple(int(v) for v in args.grid.split(",")) if args.grid else (60, 220, 85)
+            cases = [I.config_layered3d(n=n3, n_upper=max(1, round(35 * n3[2] / 85)),
+                                        space=args.space if args.space is not None else 0)]
             line["grid"] = list(n3)
+            line["space"] = "P1" if cases[0].params.space == 1 else "P0"
         else:
             cases = I.config_ensemble() if w == "ensemble" else [I.config_small() if w == "small" else I.config_layered3d()]
         probs = [c.problem for c in cases]

@@ -50,6 +50,8 @@ cudaError_t kry_from_bq(const IfPtrs& I, double* z, int n, cudaStream_t s);
 cudaError_t kry_axpby(double* y, const double* x, double a, double b, int n, cudaStream_t s);
 cudaError_t kry_dot(const double* a, const double* b, int n, double* part, cudaStream_t s);
 int kry_blocks();
+cudaError_t kry_mdot(const double* V, const double* w, int n, int nv, double* part, cudaStream_t s);
+cudaError_t kry_msub(double* w, const double* V, const double* coef, int nv, int n, cudaStream_t s);
 cudaError_t lu_inverse(const IfPtrs& I, const ElimDev* el, int nel, int* status, int variant, cudaStream_t s);
 int slab_inverse_gj_ok(int npad);
 int slab_inverse_gjr_npad(int npad);
@@ -1074,21 +1076,22 @@ static double if_target(const mrcm_handle* h) { return h->mth.ir_tol; }
 // G X = rhs, right-preconditioned by the FP32 reduction (the row scaling, the
 // sweeps and the column scaling of one refinement step), started from the
 // refined iterate.  G v is the residual kernel with x = v and a zero
-// right-hand side (it returns -G v).  Dot products: per-block partial sums
-// added on the host in a fixed order.  Ends when the library's residual test
+// right-hand side (it returns -G v).  Arnoldi by classical Gram-Schmidt
+// applied twice (all projections of a pass in one launch).  Dot products:
+// per-block partial sums added on the host in a fixed order.  Ends when the library's residual test
 // (worst member, max norm relative to the right-hand side) reaches ir_tol.
 static int krylov_interface(mrcm_handle* h, double* worst_out) {
     const int n = h->nif, m = 30, max_restarts = 20;
     cudaStream_t st = h->stream;
     const int nb = kry_blocks();
     if (!h->d_kry) {
-        if (int e = dalloc(h, &h->d_kry, (size_t)(m + 4) * n + (size_t)nb)) return e;
+        if (int e = dalloc(h, &h->d_kry, (size_t)(m + 4) * n + (size_t)(m + 1) * nb)) return e;
     }
     double* V = h->d_kry;                    // (m + 1) x n Krylov basis
     double* w = V + (size_t)(m + 1) * n;     // n
     double* u = w + n;                       // n
     double* zero = u + n;                    // n (zero right-hand side)
-    double* part = zero + n;                 // nb partial sums
+    double* part = zero + n;                 // (m + 1) x nb partial sums
     CUDA_TRY(h, cudaMemsetAsync(zero, 0, sizeof(double) * n, st));
     std::vector<double> hp(nb);
     double rhs2 = 0.0;
@@ -1099,6 +1102,20 @@ static int krylov_interface(mrcm_handle* h, double* worst_out) {
         double acc = 0.0;
         for (int i = 0; i < nb; ++i) acc += hp[i];
         *out = acc;
+        return 0;
+    };
+    // hv[i] = v_i . w for the nv vectors of V (one launch, one read back)
+    std::vector<double> hpm;
+    auto mdot = [&](const double* Vb, const double* wv, int nv, double* out) -> int {
+        hpm.resize((size_t)nv * nb);
+        CUDA_TRY(h, kry_mdot(Vb, wv, n, nv, part, st));
+        CUDA_TRY(h, cudaMemcpyAsync(hpm.data(), part, sizeof(double) * nv * nb, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        for (int i = 0; i < nv; ++i) {
+            double acc = 0.0;
+            for (int b = 0; b < nb; ++b) acc += hpm[(size_t)i * nb + b];
+            out[i] = acc;
+        }
         return 0;
     };
     // z = M^-1 v (through I.bq)
@@ -1135,11 +1152,13 @@ static int krylov_interface(mrcm_handle* h, double* worst_out) {
             J.x = u;
             CUDA_TRY(h, if_residual(J, h->d_row_member, n, 0, st));   // w = -G u
             CUDA_TRY(h, kry_axpby(w, w, 0.0, -1.0, n, st));            // w = G u
-            for (int i = 0; i <= j; ++i) {
-                double hij = 0.0;
-                if (int e = dot(w, V + (size_t)i * n, &hij)) return e;
-                H[(size_t)i * m + j] = hij;
-                CUDA_TRY(h, kry_axpby(w, V + (size_t)i * n, -hij, 1.0, n, st));
+            // classical Gram-Schmidt, applied twice (CGS2): each pass projects w
+            // on all basis vectors in one launch and one host read
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<double> hc(j + 1, 0.0);
+                if (int e = mdot(V, w, j + 1, hc.data())) return e;
+                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += hc[i];
+                CUDA_TRY(h, kry_msub(w, V, hc.data(), j + 1, n, st));
             }
             double hn2 = 0.0;
             if (int e = dot(w, w, &hn2)) return e;

@@ -25,6 +25,7 @@ __global__ void k_kry_axpby(double* y, const double* x, double a, double b, int 
 
 // per-block partial sums of a . b (grid-stride, fixed order within a block)
 constexpr int KRY_BLOCKS = 120;
+constexpr int KRY_MAXV = 32;   // vectors of one projection step at most (the restart length + 1)
 __global__ void __launch_bounds__(256) k_kry_dot(const double* a, const double* b, int n, double* part) {
     __shared__ double red[256];
     double acc = 0.0;
@@ -60,3 +61,47 @@ cudaError_t kry_dot(const double* a, const double* b, int n, double* part, cudaS
 }
 
 int kry_blocks() { return KRY_BLOCKS; }
+
+// Block partial sums of v_i . w for the nv vectors v_i = V + i n (classical
+// Gram-Schmidt: all projections of one step in one launch): part[i * KRY_BLOCKS + block].
+__global__ void __launch_bounds__(256) k_kry_mdot(const double* V, const double* w, int n, int nv, double* part) {
+    __shared__ double red[256];
+    for (int i = 0; i < nv; ++i) {
+        const double* v = V + (size_t)i * n;
+        double acc = 0.0;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += v[c] * w[c];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = 128; o; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = red[0];
+        __syncthreads();
+    }
+}
+
+// w -= sum_i c_i v_i over the nv vectors v_i = V + i n (in increasing i per entry)
+struct KryCoef {
+    double c[KRY_MAXV];
+};
+__global__ void k_kry_msub(double* w, const double* V, KryCoef cf, int nv, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double x = w[c];
+    for (int i = 0; i < nv; ++i) x -= cf.c[i] * V[(size_t)i * n + c];
+    w[c] = x;
+}
+
+cudaError_t kry_mdot(const double* V, const double* w, int n, int nv, double* part, cudaStream_t s) {
+    k_kry_mdot<<<KRY_BLOCKS, 256, 0, s>>>(V, w, n, nv, part);
+    return cudaGetLastError();
+}
+
+cudaError_t kry_msub(double* w, const double* V, const double* coef, int nv, int n, cudaStream_t s) {
+    if (nv > KRY_MAXV) return cudaErrorInvalidValue;
+    KryCoef cf{};
+    for (int i = 0; i < nv; ++i) cf.c[i] = coef[i];
+    k_kry_msub<<<(n + 255) / 256, 256, 0, s>>>(w, V, cf, nv, n);
+    return cudaGetLastError();
+}

@@ -172,6 +172,10 @@ struct mrcm_handle {
     // captured step
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr, user_stream = nullptr;
+    // the basis build's job classes run concurrently: one stream per class
+    // beyond the first, forked from and joined to the handle's stream
+    std::vector<cudaStream_t> class_streams;
+    std::vector<cudaEvent_t> class_events;   // [0] fork, [1 + k] join of class stream k
     int graph_steps = -1, graph_nit = 0;
     // reverse pass
     AdjWork adj;
@@ -759,12 +763,45 @@ int mrcm_internal_fail(mrcm_handle* h, int code, const char* msg) { return fail(
 // ---------------------------------------------------------------------------
 static int issue_basis(mrcm_handle* h) {
     Phase ph(h, 0);
-    for (auto& jc : h->jclasses) {
-        cudaError_t e = h->dim == 3
-                            ? launch_local3d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.smem, h->stream)
-                            : launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, h->stream);
+    // 2D: the classes write disjoint outputs and keep no per-CTA scratch in
+    // global memory: the largest on the handle's stream, the others on their
+    // own streams, so that their CTAs fill the SMs the largest class's last
+    // wave leaves idle (3D classes share the iterate scratch indexed by the
+    // CTA: one after the other)
+    const size_t nc = h->jclasses.size();
+    const bool concurrent = h->dim == 2 && nc > 1;
+    std::vector<size_t> order(nc);
+    for (size_t k = 0; k < nc; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const double wa = (double)h->jclasses[a].count * h->jclasses[a].smem;
+        const double wb = (double)h->jclasses[b].count * h->jclasses[b].smem;
+        return wa > wb;
+    });
+    if (concurrent) {
+        while (h->class_streams.size() < nc - 1) {
+            cudaStream_t cs = nullptr;
+            CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            h->class_streams.push_back(cs);
+        }
+        while (h->class_events.size() < nc) {
+            cudaEvent_t ev = nullptr;
+            CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            h->class_events.push_back(ev);
+        }
+        CUDA_TRY(h, cudaEventRecord(h->class_events[0], h->stream));
+        for (size_t k = 0; k + 1 < nc; ++k) CUDA_TRY(h, cudaStreamWaitEvent(h->class_streams[k], h->class_events[0], 0));
+    }
+    for (size_t r = 0; r < nc; ++r) {
+        const JobClass& jc = h->jclasses[order[r]];
+        cudaStream_t st = (r == 0 || !concurrent) ? h->stream : h->class_streams[r - 1];
+        cudaError_t e = h->dim == 3 ? launch_local3d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.smem, st)
+                                    : launch_local2d(h->P, h->mth, h->d_jobs + jc.off, jc.count, jc.bw, jc.smem, st);
         if (e != cudaSuccess) return fail(h, MRCM_ERR_CUDA, std::string("local kernel: ") + cudaGetErrorString(e));
         h->launches[0] += 1;
+    }
+    for (size_t k = 0; concurrent && k + 1 < nc; ++k) {
+        CUDA_TRY(h, cudaEventRecord(h->class_events[1 + k], h->class_streams[k]));
+        CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->class_events[1 + k], 0));
     }
     return 0;
 }
@@ -1800,6 +1837,8 @@ int mrcm_destroy(mrcm_handle* h) {
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (auto cs : h->class_streams) cudaStreamDestroy(cs);
+    for (auto ev : h->class_events) cudaEventDestroy(ev);
     delete h;
     return 0;
 }

@@ -647,6 +647,110 @@ __device__ __noinline__ void tw_warp_f32(const float* __restrict__ Sinv, const f
     tw_warp<float, BB>(Sinv, cys, w, z, BB, nb);
 }
 
+// Both twisted sweeps on two warps (FP32 row path, lines of BB cells): warp
+// 0 runs the top chain (lines 0 .. m - 1) and warp 1 the bottom chain (lines
+// nb - 1 .. m + 1), each with its rows prefetched a line ahead; after a
+// barrier of the two warps (named barrier 1) warp 0 solves the middle line m
+// from both chains' last lines, and after another the two chains run back out
+// from it.  The same operations in the same order as tw_warp (results equal
+// bit for bit), with each chain's dependent steps on its own warp.  Called by
+// threads 0 .. 63; z: 64 entries (one line input per warp).
+template <int BB>
+__device__ void tw_2warp(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* z, int nb) {
+    using Row = RowF<BB>;
+    constexpr int b = BB;
+    const int lane = threadIdx.x & 31, h = (threadIdx.x >> 5) & 1;
+    const bool act = lane < b;
+    const size_t bl = (size_t)b * Row::LD;
+    const int m = nb >> 1;
+    const int cnt = h == 0 ? m : nb - 1 - m;   // lines of this warp's chain
+    float* zz = z + 32 * h;
+    float c = 0.f;   // this lane's entry of the chain's last finished line
+    Row N, P;
+    auto jf = [&](int s) { return h == 0 ? s : nb - 1 - s; };
+    auto fwd = [&](int s, Row& C, Row& X) {
+        const int j = jf(s);
+        if (act) zz[lane] = w[j * b + lane] + (s > 0 ? cys[(h == 0 ? j - 1 : j) * b + lane] * c : 0.f);
+        __syncwarp();
+        if (s + 1 < cnt) X.load(Sinv + (size_t)jf(s + 1) * bl, lane);
+        c = C.dot(zz);
+        if (act) w[j * b + lane] = c;
+        __syncwarp();
+    };
+    if (cnt > 0) N.load(Sinv + (size_t)jf(0) * bl, lane);
+    {
+        int s = 0;
+        for (; s + 1 < cnt; s += 2) {
+            fwd(s, N, P);
+            fwd(s + 1, P, N);
+        }
+        if (s < cnt) fwd(s, N, P);
+    }
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    if (h == 0) {
+        Row L;
+        L.load(Sinv + (size_t)m * bl, lane);
+        if (act) {
+            float zm = w[m * b + lane];
+            if (m > 0) zm += cys[(m - 1) * b + lane] * w[(m - 1) * b + lane];
+            if (m < nb - 1) zm += cys[m * b + lane] * w[(m + 1) * b + lane];
+            zz[lane] = zm;
+        }
+        __syncwarp();
+        const float r = L.dot(zz);
+        if (act) w[m * b + lane] = r;
+    }
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    c = act ? w[m * b + lane] : 0.f;
+    auto jb = [&](int s) { return h == 0 ? m - 1 - s : m + 1 + s; };
+    auto bwd = [&](int s, Row& C, Row& X) {
+        const int j = jb(s);
+        float wj = 0.f;
+        if (act) {
+            zz[lane] = cys[(h == 0 ? j : j - 1) * b + lane] * c;
+            wj = w[j * b + lane];
+        }
+        __syncwarp();
+        if (s + 1 < cnt) X.load(Sinv + (size_t)jb(s + 1) * bl, lane);
+        c = wj + C.dot(zz);
+        if (act) w[j * b + lane] = c;
+        __syncwarp();
+    };
+    if (cnt > 0) N.load(Sinv + (size_t)jb(0) * bl, lane);
+    {
+        int s = 0;
+        for (; s + 1 < cnt; s += 2) {
+            bwd(s, N, P);
+            bwd(s + 1, P, N);
+        }
+        if (s < cnt) bwd(s, N, P);
+    }
+}
+
+template <int BB>
+__device__ __noinline__ void tw_2warp_f32(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w,
+                                          float* z, int nb) {
+    tw_2warp<BB>(Sinv, cys, w, z, nb);
+}
+
+// The FP32 sweeps of one right-hand side by threads 0 .. 63: two warps on the
+// row path of the box's line width where there is one, else warp 0 alone by
+// column.  zbuf: 64 entries.  The caller synchronises the block afterwards.
+__device__ void warp2_sweeps(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* zbuf,
+                             int b, int nb) {
+    switch (b) {
+        case 8: tw_2warp_f32<8>(Sinv, cys, w, zbuf, nb); return;
+        case 12: tw_2warp_f32<12>(Sinv, cys, w, zbuf, nb); return;
+        case 16: tw_2warp_f32<16>(Sinv, cys, w, zbuf, nb); return;
+        case 20: tw_2warp_f32<20>(Sinv, cys, w, zbuf, nb); return;
+        case 24: tw_2warp_f32<24>(Sinv, cys, w, zbuf, nb); return;
+        case 28: tw_2warp_f32<28>(Sinv, cys, w, zbuf, nb); return;
+        case 32: tw_2warp_f32<32>(Sinv, cys, w, zbuf, nb); return;
+        default: break;
+    }
+    if (threadIdx.x < 32) tw_warp<float, 0>(Sinv, cys, w, zbuf, b, nb);
+}
+
 // One warp solves in place (one right-hand side): the twisted sweeps, on the
 // FP32 row path of the box's line width where there is one, else by column.
 // zbuf: 64 entries of this warp.
@@ -1034,7 +1138,7 @@ __device__ int cta_solve_sc(const Box& B, const Ops& O, const float* Sinv, const
     int it = 0;
     if (warm && ((double)r0 <= tol * (double)bn || bn == 0.f)) return 0;
     for (; it < max_ir; ++it) {
-        if (tid < 32) warp_sweeps<float>(Sinv, cys, w, zw, b, nb);
+        if (tid < 64) warp2_sweeps(Sinv, cys, w, zw, b, nb);
         __syncthreads();
         for (int c = tid; c < B.n; c += nt) x[c] += f2d_bits(w[c]);
         if (tid == 0) nrm[1] = 0u;

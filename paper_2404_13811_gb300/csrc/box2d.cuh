@@ -652,9 +652,11 @@ __device__ __noinline__ void tw_warp_f32(const float* __restrict__ Sinv, const f
 // nb - 1 .. m + 1), each with its rows prefetched a line ahead; after a
 // barrier of the two warps (named barrier 1) warp 0 solves the middle line m
 // from both chains' last lines, and after another the two chains run back out
-// from it.  The same operations in the same order as tw_warp (results equal
-// bit for bit), with each chain's dependent steps on its own warp.  Called by
-// threads 0 .. 63; z: 64 entries (one line input per warp).
+// from it.  The line products of tw_warp in the same order, each chain's
+// dependent steps on its own warp; the results agree with tw_warp's to
+// rounding (the compiler may fuse the line inputs' multiply-adds
+// differently).  Called by threads 0 .. 63; z: 64 entries (one line input per
+// warp).
 template <int BB>
 __device__ void tw_2warp(const float* __restrict__ Sinv, const float* __restrict__ cys, float* w, float* z, int nb) {
     using Row = RowF<BB>;

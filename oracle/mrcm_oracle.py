@@ -445,11 +445,22 @@ def gamma_beta(prob, sd, sid, alpha, Hw):
 
 
 def mrcm_os(prob, sub, overlap, space=1, alpha_basis=1.0, alpha_smooth=1.0, n_smooth=0,
-            keep_stages=False):
+            keep_stages=False, particular="omega"):
     """MRCM-O followed by ``n_smooth`` smoothing steps (MRCM-OS).
 
-    space: 0 (P0), 1 (P1) or 'fine' (Prop. 2).  Returns a Result with the
-    assembled per-cell pressure and per-cell outward velocities."""
+    space: 0 (P0), 1 (P1) or 'fine' (Prop. 2).
+    particular: 'omega' solves the particular problem on Omega_i (Step 4,
+    Eqs. (111dbar)-(122dbar), the paper's method); 'hat' is a variant that is
+    not in the paper: the particular problem is posed on hat-Omega_i with the
+    basis operator (the same sources f, g, z and zero Robin data on
+    the sides of hat-Omega_i inside Omega) and restricted to Omega_i like the basis
+    functions, so no Omega_i operator is factored.  It shifts the affine local
+    space u = ubar + span{Phi_j} and so changes the result; for l = 0 the two
+    coincide.
+    Returns a Result with the assembled per-cell pressure and per-cell
+    outward velocities."""
+    if particular not in ("omega", "hat"):
+        raise ValueError("particular must be 'omega' or 'hat'")
     d = prob.dim
     h = prob.h
     vol = float(np.prod(h))
@@ -492,6 +503,24 @@ def mrcm_os(prob, sub, overlap, space=1, alpha_basis=1.0, alpha_smooth=1.0, n_sm
     # Step 4: particular solutions on Omega_i (Eqs. (111dbar)-(122dbar)): sources
     # f, g, z and zero Robin data on Gamma_i with beta from alpha_basis.
     for sd in subs:
+        if particular == "hat":
+            # the variant: the same sources and zero Robin data on
+            # d hat-Omega_i \ d Omega, solved with the kept basis factor; the
+            # restriction and the Gamma_i traces are taken as for the basis
+            # functions, and the face pressure pi-bar is the trace itself
+            # (the Robin data of the restriction on Gamma_i is not zero)
+            sys_hat = sd.data["sys_hat"]
+            b = box_rhs(prob, sys_hat, None, sources=True)
+            ph = sd.data["fac_hat"].solve(b)
+            counts["local_solves"][sd.index] += 1
+            uh = box_velocities(prob, sys_hat, ph, None, sources=True)
+            rmap = restriction_map(sd)
+            tr = _gamma_traces(prob, sd, ph, uh, sys_hat)
+            sd.data.update(pbar=ph[rmap], ubar=uh[rmap],
+                           Fbar={s_: tr[s_][0] for s_ in sd.sides},
+                           Ubar={s_: tr[s_][2] for s_ in sd.sides},
+                           PIbar={s_: tr[s_][1] for s_ in sd.sides})
+            continue
         sys_i = assemble_box(prob, sd.lo, sd.hi, alpha_basis, Hw)
         fac_i = BandCholesky(sys_i.A)
         counts["factorisations"][sd.index] += 1
@@ -547,7 +576,10 @@ def mrcm_os(prob, sub, overlap, space=1, alpha_basis=1.0, alpha_smooth=1.0, n_sm
                             row[col0[sdx.index] + k] += val
                         if kind == "M":
                             r -= np.dot(psi[:, m], D["Fbar"][sid])
+                        elif "PIbar" in D:
+                            r -= sign * area * np.dot(psi[:, m], D["PIbar"][sid])
                         else:
+                            # zero Robin data on Gamma_i: pi-bar = beta u-bar.n
                             r -= sign * area * np.dot(psi[:, m], beta * D["Ubar"][sid])
                     rows.append(row)
                     rhs.append(r)

@@ -1,0 +1,74 @@
+"""Pins of the oracle's particular-on-hat-Omega_i variant (not in the paper:
+the particular problem of Step 4 posed on the oversampled box with the basis
+operator and restricted to Omega_i, so that no Omega_i operator is factored).
+
+What fixes it independently of its own formulas:
+* for l = 0 hat-Omega_i = Omega_i and the variant is Step 4 itself;
+* for l > 0 a linear pressure with constant K is reproduced exactly: the
+  exact solution on hat-Omega_i is the particular solution (which now carries
+  the Dirichlet data g) plus the informed functions of its P1 Robin trace, so
+  its restriction lies in the variant's affine space and solves the interface
+  conditions; the paper's form loses this next to a Dirichlet side with g != 0
+  (its informed-space problems have homogeneous physical data), which the
+  test shows as well;
+* Eq. (12d) holds cell by cell after MRCM-O and after smoothing, sources
+  included.
+"""
+import numpy as np
+import pytest
+
+from oracle import mrcm_oracle as O
+from paper_2404_13811_gb300 import inputs as I
+
+
+def _het(n, seed):
+    prob = I.lognormal_problem(n, sigma2=2.0, corr_len=0.2, seed=seed, bc="left_right")
+    prob.f = np.random.default_rng(seed + 7).standard_normal(prob.f.shape)
+    return prob
+
+
+@pytest.mark.parametrize("space", [0, 1])
+def test_variant_equals_step4_for_l0(space):
+    prob = _het((32, 32), 3)
+    a = O.mrcm_os(prob, (8, 8), 0, space=space, particular="omega")
+    b = O.mrcm_os(prob, (8, 8), 0, space=space, particular="hat")
+    assert np.max(np.abs(a.p - b.p)) <= 1e-13 * np.max(np.abs(a.p))
+    assert np.max(np.abs(a.u - b.u)) <= 1e-13 * np.max(np.abs(a.u))
+    # no Omega_i factor in the variant: one factorisation per subdomain
+    assert set(b.counts["factorisations"]) == {1}
+    assert set(a.counts["factorisations"]) == {2}
+
+
+@pytest.mark.parametrize("overlap", [2, 4])
+def test_variant_exact_for_linear_pressure_with_overlap(overlap):
+    n = (64, 64)
+    prob = I.Problem(2, n, (1 / 64, 1 / 64), np.ones(n), np.zeros(n), *I._bc_left_right(2))
+    pf, uf = O.fine_solve(prob)
+    r = O.mrcm_os(prob, (16, 16), overlap, space=1, alpha_basis=1.0, particular="hat")
+    ep, eu = O.rel_errors(prob, r.p, r.u, pf, uf)
+    assert ep < 1e-12 and eu < 1e-12, (ep, eu)
+    r0 = O.mrcm_os(prob, (16, 16), overlap, space=1, alpha_basis=1.0)
+    assert O.rel_errors(prob, r0.p, r0.u, pf, uf)[1] > 1e-3
+
+
+def test_variant_exact_for_linear_pressure_3d():
+    n = (8, 8, 6)
+    prob = I.Problem(3, n, (1 / 8, 1 / 8, 1 / 6), np.full(n[::-1], 2.0), np.zeros(n[::-1]),
+                     *I._bc_left_right(3))
+    pf, uf = O.fine_solve(prob)
+    r = O.mrcm_os(prob, (4, 4, 3), 1, space=1, particular="hat")
+    ep, eu = O.rel_errors(prob, r.p, r.u, pf, uf)
+    assert ep < 1e-12 and eu < 1e-12, (ep, eu)
+
+
+def test_variant_conserves_mass_every_stage():
+    prob = _het((32, 32), 17)
+    r = O.mrcm_os(prob, (8, 8), 2, space=1, n_smooth=2, keep_stages=True, particular="hat")
+    for key, (p, u) in r.stages.items():
+        scale = max(np.max(np.abs(prob.f)) * np.prod(prob.h), np.max(np.abs(u)) * prob.h[0])
+        assert np.max(np.abs(O.mass_residual(prob, u))) < 1e-12 * scale, key
+
+
+def test_variant_rejects_unknown_name():
+    with pytest.raises(ValueError):
+        O.mrcm_os(_het((16, 16), 1), (8, 8), 0, particular="gamma")

@@ -50,10 +50,11 @@ def parse():
                     help="layered3d only: cells per axis as nx,ny,nz (default 60,220,85; the layer split "
                          "keeps its share of the z extent)")
     ap.add_argument("--workload", default="channel2d",
-                    choices=["channel2d", "small", "layered3d", "ensemble", "adjoint"],
+                    choices=["channel2d", "small", "layered3d", "ensemble", "adjoint", "variant"],
                     help="channel2d: the benchmark line; the others print a timing line for another "
                          "workload (64x64 quarter five-spot, 60x220x85 layered 3D, 256-member ensemble, "
-                         "256x256 gradient)")
+                         "256x256 gradient, the 512x512 channel with the particular problem on Omega_i "
+                         "and on hat-Omega_i)")
     return ap.parse_args()
 
 
@@ -119,11 +120,13 @@ def _band(sides):
     return s[0] if len(s) == 2 else s[0] * s[1]
 
 
-def algorithmic_work(cases):
+def algorithmic_work(cases, particular="omega"):
     """Arithmetic the method needs on these problems (one factorisation per
     operator, one solve per right-hand side, 2 n^3 per slab inverse):
     flops of the basis build (basis boxes, particular problems), of one
-    smoothing step, of the slab inverses, and the local right-hand sides."""
+    smoothing step, of the slab inverses, and the local right-hand sides.
+    particular="hat": the particular problem is one more solve with the
+    basis box's factor instead of an Omega_i factor and solve."""
     basis = smooth = slab = 0.0
     rhs = 0
     for case in cases:
@@ -143,7 +146,8 @@ def algorithmic_work(cases):
             nh, bh = int(np.prod(sides)), _band(sides)
             ns = sum((mi[a] > 0) + (mi[a] < M[a] - 1) for a in range(d))
             N = ns * npsi
-            basis += nh * bh * bh * (2 if extra else 1) + N * 4 * nh * bh + ni * bi * bi + 4 * ni * bi
+            part_flops = 4 * nh * bh if particular == "hat" else ni * bi * bi + 4 * ni * bi
+            basis += nh * bh * bh * (2 if extra else 1) + N * 4 * nh * bh + part_flops
             smooth += 4 * nh * bh
             rhs += N + 1
             layer[mi[-1]] = layer.get(mi[-1], 0) + N
@@ -555,6 +559,65 @@ def run_other(args):
             line[precision] = {"ms_per_step": ms, "value": cells / (ms * 1e-3), "errors_vs_oracle": errs,
                                "phase_ms_eager": {k: round(v[0], 3) for k, v in tm.items() if v[0] > 0},
                                "roofline": kr[dom], "kernel_rooflines": kr, "stats": st}
+            s.close()
+        line["clocks"] = clk.stop()
+    elif w == "variant":
+        # Step 4 as in the paper (particular problem on Omega_i) and the
+        # variant on hat-Omega_i, on the 512x512 channel workload, mixed form:
+        # time, the oracle of each form, and both against the fine solution
+        case = I.config_channel2d()
+        prob, part, pm = case.problem, case.partition, case.params
+        line.update({"cells": prob.ncells, "n_smooth": pm.n_smooth, "grid": list(prob.n), "sub": list(part.sub),
+                     "overlap": part.overlap, "space": "P1" if pm.space == 1 else "P0", "precision": "mixed",
+                     "step": "mrcm_run: the whole step replayed as one captured CUDA graph"})
+        refs, fine = {}, None
+        if not args.no_oracle:
+            from oracle import mrcm_oracle as O
+            t0 = time.perf_counter()
+            fine = O.fine_solve(prob)
+            for v in ("omega", "hat"):
+                refs[v] = O.mrcm_os(prob, part.sub, part.overlap, pm.space, pm.alpha_basis, pm.alpha_smooth,
+                                    pm.n_smooth, keep_stages=True, particular=v)
+            line["oracle"] = {"seconds": time.perf_counter() - t0,
+                              "what": "the fine solution and MRCM-OS with each particular form"}
+        clk = Clocks(dev)
+        clk.start()
+        for v in ("omega", "hat"):
+            s = MRCM(prob, part, space=pm.space, alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth,
+                     precision="mixed", stream=stream, particular=v)
+            rec = {}
+            if refs:
+                s.run(0)
+                p, u = s.fluxes()
+                rp, ru = refs[v].stages["mrcm_o"]
+                ep, eu = O.rel_errors(prob, p, u, rp, ru)
+                fp, fu = O.rel_errors(prob, p, u, *fine)
+                rec["mrcm_o"] = {"vs_oracle": {"flux_rel_l2": eu, "pressure_rel_l2": ep},
+                                 "vs_fine": {"flux_rel_l2": fu, "pressure_rel_l2": fp}}
+            s.run(pm.n_smooth, graph=True)
+            tot, _ = timer(lambda: s.run(pm.n_smooth, graph=True), args.steps, args.warmup)
+            ms = tot / args.steps
+            if refs:
+                p, u = s.fluxes()
+                ep, eu = O.rel_errors(prob, p, u, refs[v].p, refs[v].u)
+                fp, fu = O.rel_errors(prob, p, u, *fine)
+                rec[f"smooth{pm.n_smooth}"] = {"vs_oracle": {"flux_rel_l2": eu, "pressure_rel_l2": ep},
+                                               "vs_fine": {"flux_rel_l2": fu, "pressure_rel_l2": fp}}
+
+            def eager(sv):
+                sv.build_basis()
+                sv.solve_interface()
+                sv.smooth(pm.n_smooth)
+
+            tm = phase_times(s, eager, reps=1)
+            st = s.stats()
+            kr = kernel_rooflines(algorithmic_work([case], particular=v), tm, pm.n_smooth, peaks, "mixed",
+                                  st["slab_inverse"], 2)
+            rec.update({"ms_per_step": ms, "value": prob.ncells / (ms * 1e-3),
+                        "phase_ms_eager": {k: round(x[0], 3) for k, x in tm.items() if x[0] > 0},
+                        "launches_eager": {k: x[1] for k, x in tm.items() if x[1] > 0},
+                        "roofline_local_basis": kr.get("local_basis"), "stats": st})
+            line[v] = rec
             s.close()
         line["clocks"] = clk.stop()
     else:

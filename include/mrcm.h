@@ -62,6 +62,10 @@ extern "C" {
 #define MRCM_FP64 0  /* local factorisations and solves in FP64 */
 #define MRCM_MIXED 1 /* FP32 local factor/solves + FP64 residuals (iterative refinement) */
 
+/* Where the particular problem of Algorithm 1 Step 4 is posed (mrcm_params.particular). */
+#define MRCM_PARTICULAR_OMEGA 0 /* on Omega_i with its own factor (Eqs. (111dbar)-(122dbar); the paper's method) */
+#define MRCM_PARTICULAR_HAT 1   /* variant, not in the paper: on hat-Omega_i with the basis factor */
+
 /* Cartesian grid: cells per axis and cell size per axis (dim = 2 or 3). */
 typedef struct {
     int dim;
@@ -102,7 +106,21 @@ typedef struct {
  *                the interface solve).  3D local solves refine on to their
  *                residual floor: they stop at 1e-3 ir_tol, or below ir_tol
  *                once the residual no longer halves per step.
- *   max_ir       maximum refinement steps. */
+ *   max_ir       maximum refinement steps.
+ *   particular   MRCM_PARTICULAR_OMEGA (0): Step 4 as in the paper, the
+ *                particular problem (sources f, g, z, zero Robin data on
+ *                Gamma_i) on Omega_i with an Omega_i factor of its own.
+ *                MRCM_PARTICULAR_HAT (1): a variant that is not in the paper:
+ *                the same sources with zero Robin data on the sides of
+ *                hat-Omega_i inside Omega, solved with the kept basis factor
+ *                as one more right-hand side of the basis solves, and
+ *                restricted to Omega_i (pressure, Gamma_i fluxes and face
+ *                pressures) like the basis functions.  No Omega_i operator is
+ *                assembled or factored.  It shifts the affine local space and
+ *                so changes the result (for overlap 0 the two coincide).
+ *                2D only (3D: MRCM_ERR_UNSUPPORTED at create); mrcm_adjoint
+ *                and mrcm_backward return MRCM_ERR_UNSUPPORTED for it.
+ *                Other values: MRCM_ERR_BAD_INPUT. */
 typedef struct {
     int space;
     double alpha_basis;
@@ -110,6 +128,7 @@ typedef struct {
     int precision;
     double ir_tol;
     int max_ir;
+    int particular;
 } mrcm_params;
 
 typedef struct mrcm_handle mrcm_handle;

@@ -17,6 +17,7 @@ MRCM_OK = 0
 MRCM_NEUMANN, MRCM_DIRICHLET = 0, 1
 MRCM_P0, MRCM_P1 = 0, 1
 MRCM_FP64, MRCM_MIXED = 0, 1
+MRCM_PARTICULAR_OMEGA, MRCM_PARTICULAR_HAT = 0, 1
 ERRORS = {
     -1: "MRCM_ERR_BAD_INPUT", -2: "MRCM_ERR_STATE", -3: "MRCM_ERR_CUDA", -4: "MRCM_ERR_NOT_SPD",
     -5: "MRCM_ERR_NO_CONVERGENCE", -6: "MRCM_ERR_SINGULAR", -7: "MRCM_ERR_UNSUPPORTED",
@@ -38,7 +39,8 @@ class mrcm_partition(C.Structure):
 
 class mrcm_params(C.Structure):
     _fields_ = [("space", C.c_int), ("alpha_basis", C.c_double), ("alpha_smooth", C.c_double),
-                ("precision", C.c_int), ("ir_tol", C.c_double), ("max_ir", C.c_int)]
+                ("precision", C.c_int), ("ir_tol", C.c_double), ("max_ir", C.c_int),
+                ("particular", C.c_int)]
 
 
 EXPORTS = ["mrcm_create", "mrcm_create_batch", "mrcm_build_basis", "mrcm_solve_interface",
@@ -120,7 +122,7 @@ def make_structs(dim, n, h, bc_kind, bc_value, sub, overlap):
     return g, b, p
 
 
-def make_params(space, alpha_basis, alpha_smooth, precision, ir_tol=1e-12, max_ir=30):
+def make_params(space, alpha_basis, alpha_smooth, precision, ir_tol=1e-12, max_ir=30, particular=0):
     q = mrcm_params()
     q.space = int(space)
     q.alpha_basis = float(alpha_basis)
@@ -128,6 +130,7 @@ def make_params(space, alpha_basis, alpha_smooth, precision, ir_tol=1e-12, max_i
     q.precision = int(precision)
     q.ir_tol = float(ir_tol)
     q.max_ir = int(max_ir)
+    q.particular = int(particular)
     return q
 
 

@@ -271,6 +271,10 @@ int check_inputs(mrcm_handle* h, const mrcm_grid* g, const mrcm_bc* bc, const mr
     if (!(pr->alpha_basis > 0.0) || !(pr->alpha_smooth > 0.0))
         return fail(h, MRCM_ERR_BAD_INPUT, "alpha must be positive");
     if (pr->max_ir < 1) return fail(h, MRCM_ERR_BAD_INPUT, "max_ir must be >= 1");
+    if (pr->particular != MRCM_PARTICULAR_OMEGA && pr->particular != MRCM_PARTICULAR_HAT)
+        return fail(h, MRCM_ERR_BAD_INPUT, "bad particular");
+    if (pr->particular == MRCM_PARTICULAR_HAT && g->dim != 2)
+        return fail(h, MRCM_ERR_UNSUPPORTED, "the particular problem on hat-Omega_i is available in 2D");
     return 0;
 }
 
@@ -451,6 +455,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     h->mth.ir_tol = h->prm.ir_tol > 0 ? h->prm.ir_tol : 1e-12;
     h->mth.max_ir = prec == MRCM_FP64 ? 1 : h->prm.max_ir;
     h->mth.same_alpha = h->prm.alpha_basis == h->prm.alpha_smooth;
+    h->mth.part_hat = h->prm.particular == MRCM_PARTICULAR_HAT;
     // The smoothing kernel waits up to 2^31 cycles for its staged copy.  For
     // the failure-detection test only, MRCM_TEST_FIRST_WAIT_CYCLES = N > 0
     // makes its first wait one of N cycles for a barrier nothing arrives at:
@@ -489,15 +494,18 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
             return fail(h, MRCM_ERR_UNSUPPORTED, "2D boxes wider than 32 cells along x are not supported");
         fac_stride = std::max(fac_stride, spack_bytes(prec, bx, by) / tsz);   // smoothing packs, 16-byte multiples
         dsc_stride = std::max(dsc_stride, (size_t)bx * by);
-        auto add = [&](int type, int nx, int ny, int nrhs) {
+        // with the particular problem on hat-Omega_i it is one more
+        // right-hand side of the basis job (kept in global memory, so the
+        // basis box needs no more shared memory)
+        const bool hat = h->mth.part_hat;
+        auto add = [&](int type, int nx, int ny, int nrhs, bool staged) {
             const int bw = local2d_class(prec, nx);
             byw[bw].push_back(Job{s, type});
-            smem_w[bw] = std::max(smem_w[bw],
-                                  local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1), type == JOB_PART));
+            smem_w[bw] = std::max(smem_w[bw], local2d_smem(prec, nx, ny, std::max(std::min(nrhs, 4), 1), staged));
         };
-        add(JOB_BASIS, bx, by, sd.nbasis);
-        add(JOB_PART, ix, iy, 1);
-        if (!h->mth.same_alpha) add(JOB_SFACT, bx, by, 0);
+        add(JOB_BASIS, bx, by, sd.nbasis + (hat ? 1 : 0), false);
+        if (!hat) add(JOB_PART, ix, iy, 1, true);
+        if (!h->mth.same_alpha) add(JOB_SFACT, bx, by, 0, false);
         h->smooth_smem = std::max(h->smooth_smem, smooth2d_smem(prec, bx, by));
     }
     if (h->smooth_smem > 227 * 1024) return fail(h, MRCM_ERR_UNSUPPORTED, "subdomain box too large for shared memory");
@@ -543,6 +551,8 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
         if ((e = dalloc(h, &d_xs, slots * 4 * dsc_stride))) return e;
     }
     if ((e = dalloc(h, &h->d_dsc, dsc_stride * nitems))) return e;
+    double* d_bsrc = nullptr;
+    if (h->mth.part_hat && (e = dalloc(h, &d_bsrc, dsc_stride * nitems))) return e;
     if ((e = dalloc(h, &h->d_Psi, (size_t)nitems * h->nbasis_max * h->ncell_i_max))) return e;
     if ((e = dalloc(h, &h->d_Ug, (size_t)nitems * h->nbasis_max * MRCM_MAXSIDE * h->side_max))) return e;
     if ((e = dalloc(h, &h->d_pbar, (size_t)nitems * h->ncell_i_max))) return e;
@@ -593,6 +603,7 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
     P.xs_stride = (long long)(4 * dsc_stride);
     P.dsc = h->d_dsc;
     P.dsc_stride = (long long)dsc_stride;
+    P.bsrc = d_bsrc;
     P.Psi = h->d_Psi;
     P.Ug = h->d_Ug;
     P.pbar = h->d_pbar;
@@ -1696,6 +1707,8 @@ static int adjoint_body(mrcm_handle* h, const double* gp, const double* gu, doub
     if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_adjoint needs a solution");
     if (h->dim != 2) return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint is available for 2D problems");
+    if (h->mth.part_hat)
+        return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint is available for the particular problem on Omega_i");
     for (auto& md : h->mem)
         if (md.pure_neumann)
             return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint needs Dirichlet data on some side of every member");

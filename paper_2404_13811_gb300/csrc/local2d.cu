@@ -40,7 +40,12 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
         else setup_box(B, md, sd.loh, sd.hih, job.type == JOB_SFACT ? Mth.alpha_s : Mth.alpha_b);
     }
     __syncthreads();
-    const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (job.type == JOB_PART ? 1 : 0);
+    // right-hand sides: the basis functions, or the particular problem on
+    // Omega_i; with the particular problem on hat-Omega_i (a variant) it is
+    // the basis job's last right-hand side, k = nbasis, its vector kept in
+    // global memory (the basis box has no shared memory left for it)
+    const bool hat_part = job.type == JOB_BASIS && Mth.part_hat;
+    const int nrhs = job.type == JOB_BASIS ? sd.nbasis + (hat_part ? 1 : 0) : (job.type == JOB_PART ? 1 : 0);
     Carve<T> C = carve<T>(smem, B.nx, B.ny, nrhs > 0 ? min(nrhs, NWARP) : 1, job.type == JOB_PART);
     if (!mrcm_check(P.status, C.end <= mrcm_dyn_smem_bytes(), 1, (long long)C.end)) return;   // uniform
     if (threadIdx.x == 0) { C.flags[0] = 0; C.flags[1] = 0; }
@@ -96,7 +101,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
         T* w = C.W + (size_t)warp * B.n;
         int it;
         int sk = -1, mk = 0;
-        if (job.type == JOB_BASIS) {
+        const bool part = job.type == JOB_PART || k >= sd.nbasis;   // the particular problem
+        if (!part) {
             // k -> (side, m): sides of Gamma_i in increasing id, npsi functions each
             int q = k / npsi;
             mk = k % npsi;
@@ -124,17 +130,18 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
             }
         } else {
             // the particular problem: fixed right-hand side staged once (b~ in the mixed form)
+            double* bs = hat_part ? P.bsrc + (size_t)job.item * P.dsc_stride : C.bsrc;
             for (int c = lane; c < B.n; c += 32) {
                 const int i = c % B.nx, j = c / B.nx;
-                C.bsrc[c] = C.O.dsc[c] * source_rhs(B, C.O, fm, md.n[0], vol, ax, ay, nullptr, i, j);
+                bs[c] = C.O.dsc[c] * source_rhs(B, C.O, fm, md.n[0], vol, ax, ay, nullptr, i, j);
             }
             __syncwarp();
             if constexpr (mixed) {
-                RhsScStored rs{C.bsrc};
+                RhsScStored rs{bs};
                 it = warp_solve_sc<RhsScStored, EX ? BW : 0>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol,
                                                               Mth.max_ir, &C.flags[1]);
             } else {
-                RhsStored rs{C.bsrc};
+                RhsStored rs{bs};
                 it = warp_solve<T, RhsStored>(B, C.O, C.Sinv, C.cys, x, w, zb, rs, Mth.ir_tol, Mth.max_ir,
                                               &C.flags[1]);
             }
@@ -147,8 +154,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
         nsolve += it;
         __syncwarp();
         // ---- outputs: restriction to Omega_i and Gamma_i traces (Eq. (informed_space)) ----
-        const int slot = (job.type == JOB_BASIS) ? k : P.nbasis_max;
-        double* psi_out = (job.type == JOB_BASIS)
+        const int slot = !part ? k : P.nbasis_max;
+        double* psi_out = !part
                               ? P.Psi + ((size_t)job.item * P.nbasis_max + k) * P.ncell_i_max
                               : P.pbar + (size_t)job.item * P.ncell_i_max;
         for (int c = lane; c < nIx * nIy; c += 32) {
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
             const double rl = 1.0 / (double)len;
             const double area = a == 0 ? ax : ay;
             const double rarea = a == 0 ? rax : ray;
-            double* ug = (job.type == JOB_BASIS)
+            double* ug = !part
                              ? P.Ug + (((size_t)job.item * P.nbasis_max + k) * MRCM_MAXSIDE + sid) * P.side_max
                              : P.ubg + ((size_t)job.item * MRCM_MAXSIDE + sid) * P.side_max;
             double fmv[3] = {0, 0, 0}, pmv[3] = {0, 0, 0};
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) k_local2d(DevPtrs P, MethodDev 
                     const int pos = a == 0 ? j : i;
                     const int blen = a == 0 ? B.ny : B.nx;
                     double lam = 0.0;
-                    if (job.type == JOB_BASIS && sid == sk) lam = psi_val(mk, pos, blen, B.rlen[sid]);
+                    if (!part && sid == sk) lam = psi_val(mk, pos, blen, B.rlen[sid]);
                     uo = C.O.bT[side_off(B, sid) + pos] * (pL - lam) * rarea;
                     if (job.type == JOB_PART) pi = C.O.bB[side_off(B, sid) + pos] * uo;  // beta ubar.n
                     else pi = pL - uo * hkL;

@@ -86,6 +86,7 @@ struct DevPtrs {
     long long xs_stride;
     double* dsc;         // Jacobi scaling of the smoothing operator (mixed form)
     long long dsc_stride;
+    double* bsrc;        // 2D, particular problem on hat-Omega_i: its right-hand side [item][dsc_stride]
     // basis data
     double* Psi;         // [item][nbasis_max][ncell_i_max]
     double* Ug;          // [item][nbasis_max][2d][side_max]
@@ -103,6 +104,7 @@ struct MethodDev {
     double ir_tol;
     int max_ir;
     int same_alpha;
+    int part_hat;      // the particular problem on hat-Omega_i (one more right-hand side of the basis job)
     long long wait0;   // cycle limit of the first wait for a staged copy in the 2D smoothing kernel
 };
 

@@ -22,11 +22,14 @@ class MRCM:
     problems: one object (or a list) with attributes dim, n, h, K, f,
     bc_kind, bc_value (see ``inputs.Problem``); partitions: matching
     (sub, overlap) objects; params: space, alpha_basis, alpha_smooth.
-    precision: "fp64" or "mixed".  K / f may be numpy arrays (copied from the
-    host) or CUDA tensors (copied on the device)."""
+    precision: "fp64" or "mixed".  particular: "omega" (Step 4 on Omega_i,
+    the paper's method) or "hat" (the variant on hat-Omega_i with the basis
+    factor; 2D).  K / f may be numpy arrays (copied from the host) or CUDA
+    tensors (copied on the device)."""
 
     def __init__(self, problems, partitions, space=1, alpha_basis=1.0, alpha_smooth=1.0,
-                 precision="fp64", ir_tol=1e-12, max_ir=30, stream=None, device_inputs=False):
+                 precision="fp64", ir_tol=1e-12, max_ir=30, stream=None, device_inputs=False,
+                 particular="omega"):
         import torch
         single = not isinstance(problems, (list, tuple))
         self.problems = [problems] if single else list(problems)
@@ -34,7 +37,10 @@ class MRCM:
             else list(partitions)
         self.dim = self.problems[0].dim
         prec = L.MRCM_FP64 if precision == "fp64" else L.MRCM_MIXED
-        self.params = L.make_params(space, alpha_basis, alpha_smooth, prec, ir_tol, max_ir)
+        if particular not in ("omega", "hat"):
+            raise ValueError("particular must be 'omega' or 'hat'")
+        self.params = L.make_params(space, alpha_basis, alpha_smooth, prec, ir_tol, max_ir,
+                                    L.MRCM_PARTICULAR_HAT if particular == "hat" else L.MRCM_PARTICULAR_OMEGA)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         grids, bcs, pts, Ks, fs = [], [], [], [], []
         self._keep = []

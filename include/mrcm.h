@@ -118,8 +118,8 @@ typedef struct {
  *                pressures) like the basis functions.  No Omega_i operator is
  *                assembled or factored.  It shifts the affine local space and
  *                so changes the result (for overlap 0 the two coincide).
- *                2D only (3D: MRCM_ERR_UNSUPPORTED at create); mrcm_adjoint
- *                and mrcm_backward return MRCM_ERR_UNSUPPORTED for it.
+ *                2D and 3D; mrcm_adjoint and mrcm_backward return
+ *                MRCM_ERR_UNSUPPORTED for it.
  *                Other values: MRCM_ERR_BAD_INPUT. */
 typedef struct {
     int space;

@@ -273,8 +273,6 @@ int check_inputs(mrcm_handle* h, const mrcm_grid* g, const mrcm_bc* bc, const mr
     if (pr->max_ir < 1) return fail(h, MRCM_ERR_BAD_INPUT, "max_ir must be >= 1");
     if (pr->particular != MRCM_PARTICULAR_OMEGA && pr->particular != MRCM_PARTICULAR_HAT)
         return fail(h, MRCM_ERR_BAD_INPUT, "bad particular");
-    if (pr->particular == MRCM_PARTICULAR_HAT && g->dim != 2)
-        return fail(h, MRCM_ERR_UNSUPPORTED, "the particular problem on hat-Omega_i is available in 2D");
     return 0;
 }
 
@@ -481,12 +479,17 @@ static int create_impl(int count, const mrcm_grid* grids, const double* const* K
             if (!stage3_aligned(prec, bx, by, bz) || !stage3_aligned(prec, ix, iy, iz))
                 return fail(h, MRCM_ERR_UNSUPPORTED, "3D box layout breaks the 16-byte rule of the bulk copies");
             fac_stride = std::max(fac_stride, (factor3_entries(bx, by, bz) + 3) & ~size_t(3));
-            part_stride = std::max(part_stride, (factor3_entries(ix, iy, iz) + 3) & ~size_t(3));
             dsc_stride = std::max(dsc_stride, (size_t)bx * by * bz);
             byw[0].push_back(Job{s, JOB_BASIS});
-            byw[0].push_back(Job{s, JOB_PART});
+            smem_w[0] = std::max(smem_w[0], local3d_smem(prec, bx, by, bz, false));
+            if (!h->mth.part_hat) {
+                // the particular problem on Omega_i, with its own factor (on
+                // hat-Omega_i it is the basis job's last right-hand side)
+                part_stride = std::max(part_stride, (factor3_entries(ix, iy, iz) + 3) & ~size_t(3));
+                byw[0].push_back(Job{s, JOB_PART});
+                smem_w[0] = std::max(smem_w[0], local3d_smem(prec, ix, iy, iz, true));
+            }
             if (!h->mth.same_alpha) byw[0].push_back(Job{s, JOB_SFACT});
-            smem_w[0] = std::max({smem_w[0], local3d_smem(prec, bx, by, bz, false), local3d_smem(prec, ix, iy, iz, true)});
             h->smooth_smem = std::max(h->smooth_smem, smooth3d_smem(prec, bx, by, bz));
             continue;
         }

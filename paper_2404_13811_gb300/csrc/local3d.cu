@@ -543,11 +543,15 @@ __device__ double source_rhs3(const Box3& B, const Ops3& O, const MemberDev& md,
     return r;
 }
 
+// Right-hand sides of a group of basis solves; sk[q] < 0 marks the particular
+// problem on hat-Omega_i (a variant of Step 4), whose vector bs is stored.
 struct RhsBasis3 {
     const Box3* B;
     const double* bT;
+    const double* bs;
     int sk[NR3], mk[NR3];
     __device__ double operator()(int q, int t) const {
+        if (sk[q] < 0) return bs[t];
         const int sid = sk[q], a = sid >> 1;
         int c[3];
         bcoord(*B, t, c);
@@ -727,14 +731,19 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
         atomicOr(&P.status[0], ST_NOT_SPD);
         atomicExch(&P.status[2], job.item);
     }
-    const int nrhs = job.type == JOB_BASIS ? sd.nbasis : (part ? 1 : 0);
+    // with the particular problem on hat-Omega_i (a variant) it is the basis
+    // job's last right-hand side, k = nbasis, its vector kept in global memory
+    const bool hat_part = job.type == JOB_BASIS && Mth.part_hat;
+    const int nrhs = job.type == JOB_BASIS ? sd.nbasis + (hat_part ? 1 : 0) : (part ? 1 : 0);
     if (nrhs == 0) return;
 
     const int npsi = Mth.npsi;
     const double vol = md.h[0] * md.h[1] * md.h[2];
     const double* fm = P.f + md.cell_off;
-    if (part) {
-        for (int t = threadIdx.x; t < B.nc; t += blockDim.x) C.bsrc[t] = source_rhs3(B, C.O, md, fm, nullptr, t);
+    double* bsg = hat_part ? P.bsrc + (size_t)job.item * P.dsc_stride : nullptr;
+    if (part || hat_part) {
+        double* bs = part ? C.bsrc : bsg;
+        for (int t = threadIdx.x; t < B.nc; t += blockDim.x) bs[t] = source_rhs3(B, C.O, md, fm, nullptr, t);
         __syncthreads();
     }
     int nI[3], off[3];
@@ -750,12 +759,14 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
         RhsBasis3 rb;
         rb.B = &B;
         rb.bT = C.O.bT;
+        rb.bs = bsg;
         if (!part) {
             for (int q = 0; q < nr; ++q) {
                 const int k = k0 + q;
                 int qq = k / npsi;
                 rb.mk[q] = k % npsi;
-                rb.sk[q] = 0;
+                rb.sk[q] = k >= sd.nbasis ? -1 : 0;
+                if (k >= sd.nbasis) continue;
                 for (int sid = 0; sid < 6; ++sid)
                     if (sd.side_mask & (1 << sid)) {
                         if (qq == 0) { rb.sk[q] = sid; break; }
@@ -776,8 +787,9 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
         for (int t = threadIdx.x; t < NR3 * 6 * 3 * 2; t += blockDim.x) C.macc[t] = 0.0;
         for (int q = 0; q < nr; ++q) {
             const double* x = C.X + (size_t)q * B.nc;
-            double* psi_out = part ? P.pbar + (size_t)job.item * P.ncell_i_max
-                                   : P.Psi + ((size_t)job.item * P.nbasis_max + k0 + q) * P.ncell_i_max;
+            const bool pq = part || k0 + q >= sd.nbasis;   // the particular problem
+            double* psi_out = pq ? P.pbar + (size_t)job.item * P.ncell_i_max
+                                 : P.Psi + ((size_t)job.item * P.nbasis_max + k0 + q) * P.ncell_i_max;
             for (int ci = threadIdx.x; ci < nIc; ci += blockDim.x) {
                 int c[3];
                 c[0] = ci % nI[0] + off[0];
@@ -790,6 +802,7 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
         for (int q = 0; q < nr; ++q) {
             const double* x = C.X + (size_t)q * B.nc;
             const int k = k0 + q;
+            const bool pq = part || k >= sd.nbasis;
             for (int sid = 0; sid < 6; ++sid) {
                 if (!(sd.side_mask & (1 << sid))) continue;
                 const int a = sid >> 1;
@@ -797,8 +810,8 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
                 const int ls = nI[ts], lt = nI[tt];
                 const double area = vol / md.h[a];
                 const double rarea = 1.0 / area;
-                double* ug = part ? P.ubg + ((size_t)job.item * MRCM_MAXSIDE + sid) * P.side_max
-                                  : P.Ug + (((size_t)job.item * P.nbasis_max + k) * MRCM_MAXSIDE + sid) * P.side_max;
+                double* ug = pq ? P.ubg + ((size_t)job.item * MRCM_MAXSIDE + sid) * P.side_max
+                                : P.Ug + (((size_t)job.item * P.nbasis_max + k) * MRCM_MAXSIDE + sid) * P.side_max;
                 for (int e = threadIdx.x; e < ls * lt; e += blockDim.x) {
                     int c[3];
                     c[a] = (sid & 1) ? off[a] + nI[a] - 1 : off[a];
@@ -820,7 +833,7 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
                     } else {
                         const int eb = B.soff[sid] + side_e(B, sid, c);
                         double lam = 0.0;
-                        if (!part && sid == rb.sk[q])
+                        if (!pq && sid == rb.sk[q])
                             lam = psi3(rb.mk[q], c[ts], B.n[ts], c[tt], B.n[tt]);
                         uo = C.O.bT[eb] * (pL - lam) * rarea;
                         pi = part ? C.O.bB[eb] * uo : pL - uo * hkL;
@@ -839,7 +852,7 @@ __global__ void __launch_bounds__(T3) k_local3d(DevPtrs P, MethodDev Mth, const 
         for (int t = threadIdx.x; t < nr * 6 * npsi * 2; t += blockDim.x) {
             const int w = t & 1, m = (t >> 1) % npsi, sid = ((t >> 1) / npsi) % 6, q = (t >> 1) / (npsi * 6);
             if (!(sd.side_mask & (1 << sid))) continue;
-            const int slot = part ? P.nbasis_max : k0 + q;
+            const int slot = (part || k0 + q >= sd.nbasis) ? P.nbasis_max : k0 + q;
             P.mom[((((size_t)job.item * (P.nbasis_max + 1) + slot) * MRCM_MAXSIDE + sid) * npsi + m) * 2 + w] =
                 C.macc[((q * 6 + sid) * 3 + m) * 2 + w];
         }

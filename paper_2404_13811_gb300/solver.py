@@ -24,7 +24,7 @@ class MRCM:
     (sub, overlap) objects; params: space, alpha_basis, alpha_smooth.
     precision: "fp64" or "mixed".  particular: "omega" (Step 4 on Omega_i,
     the paper's method) or "hat" (the variant on hat-Omega_i with the basis
-    factor; 2D).  K / f may be numpy arrays (copied from the host) or CUDA
+    factor).  K / f may be numpy arrays (copied from the host) or CUDA
     tensors (copied on the device)."""
 
     def __init__(self, problems, partitions, space=1, alpha_basis=1.0, alpha_smooth=1.0,

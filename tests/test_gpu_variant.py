@@ -121,6 +121,36 @@ def test_hat_particular_full_size_channel_512_captured_step():
     assert st["subdomains"] == 1024
 
 
+CASES3 = [
+    # n, sub, overlap, space, alpha_basis, alpha_smooth, n_smooth, bc
+    ((20, 16, 12), (10, 8, 6), 2, 0, 1.0, 1.0, 2, "left_right"),
+    ((24, 12, 16), (8, 6, 8), 1, 1, 1.0, 1.0, 1, "left_right"),
+    ((16, 16, 8), (8, 8, 4), 1, 0, 1.0, 1.0, 2, "noflow"),
+    ((16, 12, 12), (8, 6, 6), 1, 1, 0.5, 1.0, 1, "left_right"),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(len(CASES3)))
+def test_hat_particular_3d(case, precision):
+    """3D boxes (plane-block factor): the particular problem is the basis
+    job's last right-hand side in its group of four; random sources, P0 and
+    P1, pure Neumann, Step 6."""
+    from paper_2404_13811_gb300.solver import MRCM
+    n, sub, ov, space, ab, as_, ns, bc = CASES3[case]
+    prob = I.lognormal_problem(n, sigma2=2.0, corr_len=0.2, seed=170 + case, bc=bc)
+    prob.f = np.random.default_rng(173 + case).standard_normal(prob.f.shape)
+    if bc == "noflow":
+        prob.f -= prob.f.mean()
+    ref = O.mrcm_os(prob, sub, ov, space, ab, as_, ns, particular="hat")
+    s = MRCM(prob, I.Partition(sub, ov), space=space, alpha_basis=ab, alpha_smooth=as_, precision=precision,
+             particular="hat")
+    s.run(ns)
+    p, u = s.fluxes()
+    s.close()
+    _compare(prob, p, u, ref.p, ref.u, TOL[precision], f"3D case {case} {precision}")
+
+
 def test_hat_particular_has_no_adjoint():
     from paper_2404_13811_gb300 import _lib as L
     case = _case((32, 32), (16, 16), 2, 1, seed=7)

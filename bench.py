@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--grid", default=None,
                     help="layered3d only: cells per axis as nx,ny,nz (default 60,220,85; the layer split "
                          "keeps its share of the z extent)")
+    ap.add_argument("--particular", default="omega", choices=["omega", "hat"],
+                    help="small, layered3d, ensemble: the particular problem of Step 4 on Omega_i (the paper) "
+                         "or on hat-Omega_i (the variant)")
     ap.add_argument("--workload", default="channel2d",
                     choices=["channel2d", "small", "layered3d", "ensemble", "adjoint", "variant"],
                     help="channel2d: the benchmark line; the others print a timing line for another "
@@ -512,7 +515,7 @@ def run_other(args):
         pm = cases[0].params
         cells = sum(p.ncells for p in probs)
         dim = probs[0].dim
-        line.update({"members": len(cases), "cells": cells, "n_smooth": pm.n_smooth,
+        line.update({"members": len(cases), "cells": cells, "n_smooth": pm.n_smooth, "particular": args.particular,
                      "step": "mrcm_run: the whole step replayed as one captured CUDA graph"})
         # oracle check: every member of the small and 3D workloads; a seeded
         # subset of 4 members of the ensemble
@@ -526,15 +529,17 @@ def run_other(args):
             for m in check:
                 c = cases[m]
                 refs[m] = O.mrcm_os(c.problem, c.partition.sub, c.partition.overlap, c.params.space,
-                                    c.params.alpha_basis, c.params.alpha_smooth, c.params.n_smooth)
+                                    c.params.alpha_basis, c.params.alpha_smooth, c.params.n_smooth,
+                                    particular=args.particular)
             line["oracle"] = {"members_checked": check, "seconds": time.perf_counter() - t0,
                               "subset": "seeded subset of 4 members" if w == "ensemble" else "all members"}
-        work = algorithmic_work(cases)
+        work = algorithmic_work(cases, particular=args.particular)
         clk = Clocks(dev)
         clk.start()
         for precision in ("mixed", "fp64"):
             s = MRCM(probs if len(probs) > 1 else probs[0], parts if len(parts) > 1 else parts[0], space=pm.space,
-                     alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth, precision=precision, stream=stream)
+                     alpha_basis=pm.alpha_basis, alpha_smooth=pm.alpha_smooth, precision=precision, stream=stream,
+                     particular=args.particular)
             s.run(pm.n_smooth, graph=True)
             tot, _ = timer(lambda: s.run(pm.n_smooth, graph=True), args.steps, args.warmup)
             ms = tot / args.steps

@@ -159,8 +159,11 @@ int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
  * Eq. (oversampling_problem), keep the restriction of each solution to
  * Omega_i (Remark, Sec. 2.2) and its flux / face-pressure traces on Gamma_i,
  * factor the Omega_i operator and solve the particular problem of Eqs.
- * (111dbar)-(122dbar).  When alpha_smooth != alpha_basis it also factors the
- * smoothing operator (Step 6). */
+ * (111dbar)-(122dbar) (with mrcm_params.particular = MRCM_PARTICULAR_HAT the
+ * particular problem is instead one more right-hand side of the hat-Omega_i
+ * solves, restricted like them, and no Omega_i operator is factored).  When
+ * alpha_smooth != alpha_basis it also factors the smoothing operator
+ * (Step 6). */
 int mrcm_build_basis(mrcm_handle* h);   /* any stage; restarts the pipeline */
 
 /* Algorithm 1, Step 5: assembles the interface rows of Eqs.
@@ -252,7 +255,8 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
  * use); the interface system is solved transposed with its FP32 slab factors
  * and FP64 refinement.  Leaves the current solution unchanged.
  * MRCM_ERR_UNSUPPORTED for a member with no Dirichlet side (its pressure is
- * fixed only up to a constant).  Needs a solution (MRCM_ERR_STATE). */
+ * fixed only up to a constant), for 3D problems and for the particular
+ * problem on hat-Omega_i.  Needs a solution (MRCM_ERR_STATE). */
 int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs);
 
 /* The same reverse pass with the seeds in (velocity, pressure) order and host

@@ -28,6 +28,11 @@ coefficient c, dL/dc = -mu^T (dA/dc) p + mu^T (db/dc) + gu . dV/dc.
 
 Pure-Neumann problems are not differentiated here (their interface solve is
 a minimum-norm least-squares solution): use Dirichlet data on some side.
+
+particular="hat" differentiates the oracle's variant in which the
+particular problem is posed on hat-Omega_i with the basis operator: it then
+runs backwards like a basis problem (sources instead of Robin data, its face
+pressure pi-bar = p - u.n h / (2K) in the pressure rows).
 """
 from __future__ import annotations
 
@@ -144,7 +149,8 @@ def _add_beta(prob, sd, sid, alpha, Hw, gbeta, gK):
     np.add.at(gK, go, gbeta * do)
 
 
-def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smooth, gp, gu):
+def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smooth, gp, gu,
+                    particular="omega"):
     """Returns (Result of the forward run, dL/dlog K (ncells,)) for the seeds
     gp (ncells,) and gu (ncells, 2d) of a scalar loss of the returned (p, u)."""
     if O.is_pure_neumann(prob):
@@ -154,7 +160,8 @@ def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smoo
     vol = float(np.prod(h))
     Hw = tuple(sub[a] * h[a] for a in range(d))
     Kf = prob.K.reshape(-1)
-    res = O.mrcm_os(prob, sub, overlap, space, alpha_basis, alpha_smooth, 0)
+    hat = particular == "hat"
+    res = O.mrcm_os(prob, sub, overlap, space, alpha_basis, alpha_smooth, 0, particular=particular)
     subs, col0, X, G = res.subs, res.col0, res.X, res.G
     _, M = O.decompose(prob, sub, overlap)
 
@@ -234,6 +241,7 @@ def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smoo
         sd.data["gPHI"] = [{s_: np.zeros(len(sd.data["F"][k][s_])) for s_ in sd.sides} for k in range(nk)]
         sd.data["gFbar"] = {s_: np.zeros(len(sd.data["Fbar"][s_])) for s_ in sd.sides}
         sd.data["gUbar"] = {s_: np.zeros(len(sd.data["Fbar"][s_])) for s_ in sd.sides}
+        sd.data["gPIbar"] = {s_: np.zeros(len(sd.data["Fbar"][s_])) for s_ in sd.sides}
     row = 0
     for a in range(d):
         for sd in subs:
@@ -264,6 +272,8 @@ def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smoo
                                 gbeta += gg * sign * area * psi[:, m] * uk
                         if kind == "M":
                             D["gFbar"][sid] += -grhs[row] * psi[:, m]
+                        elif hat:
+                            D["gPIbar"][sid] += -grhs[row] * sign * area * psi[:, m]
                         else:
                             D["gUbar"][sid] += -grhs[row] * sign * area * psi[:, m] * beta
                             gbeta += -grhs[row] * sign * area * psi[:, m] * D["Ubar"][sid]
@@ -311,8 +321,37 @@ def mrcm_os_adjoint(prob, sub, overlap, space, alpha_basis, alpha_smooth, n_smoo
                 box_adjoint(prob, sys_hat, fac, pk, lam, False, lgp, lgu, alpha_basis, Hw, gK)
                 k += 1
 
+    # ---- particular problems on hat-Omega_i (the variant), backwards ----
+    for sd in (subs if hat else ()):
+        D = sd.data
+        sys_hat, fac = D["sys_hat"], D["fac_hat"]
+        nloc = len(sys_hat.Kc)
+        rmap = O.restriction_map(sd)
+        loc_shape = [sd.hi_hat[b] - sd.lo_hat[b] for b in range(d)]
+        st = O.strides(loc_shape)
+        sgp, sgu = seeds_p[sd.index]
+        ph = fac.solve(O.box_rhs(prob, sys_hat, None, sources=True))
+        uh = O.box_velocities(prob, sys_hat, ph, None, sources=True)
+        lgp = np.zeros(nloc)
+        lgu = np.zeros((nloc, 2 * d))
+        lgp[rmap] = sgp
+        lgu[rmap] = sgu
+        # traces F-bar = a u.n, pi-bar = p - u.n h / (2K)
+        for s_ in sd.sides:
+            a_ = s_ // 2
+            area = vol / h[a_]
+            cl = O.gamma_faces(sd, s_)
+            loc = sum((cl[:, b] - sd.lo_hat[b]) * st[b] for b in range(d))
+            gi = O.flat_index(cl, prob.n)
+            uo = uh[loc, s_]
+            gPI = D["gPIbar"][s_]
+            np.add.at(lgu, (loc, np.full(len(loc), s_)), area * D["gFbar"][s_] - gPI * h[a_] / (2.0 * Kf[gi]))
+            np.add.at(lgp, loc, gPI)
+            np.add.at(gK, gi, gPI * uo * h[a_] / (2.0 * Kf[gi] ** 2))
+        box_adjoint(prob, sys_hat, fac, ph, None, True, lgp, lgu, alpha_basis, Hw, gK)
+
     # ---- particular problems on Omega_i, backwards (Eqs. (111dbar)-(122dbar)) ----
-    for sd in subs:
+    for sd in (() if hat else subs):
         D = sd.data
         sys_i = O.assemble_box(prob, sd.lo, sd.hi, alpha_basis, Hw)
         fac_i = O.BandCholesky(sys_i.A)

@@ -100,3 +100,27 @@ def test_adjoint_refuses_pure_neumann():
     with pytest.raises(NotImplementedError):
         AD.mrcm_os_adjoint(prob, (16, 16), 2, 0, 1.0, 1.0, 0,
                            np.zeros(prob.ncells), np.zeros((prob.ncells, 4)))
+
+
+def _complex_step_variant(prob, j, args, wp, wu, t=1e-30):
+    Kc = prob.K.astype(complex)
+    Kc.reshape(-1)[j] *= np.exp(1j * t)
+    pc = dataclasses.replace(prob, K=Kc)
+    return np.imag(_loss(O.mrcm_os(pc, *args, particular="hat"), wp, wu)) / t
+
+
+@pytest.mark.parametrize("space,overlap,n_smooth,alphas", [
+    (1, 2, 2, (1.0, 1.0)),
+    (0, 2, 1, (0.5, 2.0)),
+])
+def test_adjoint_of_hat_particular_variant_matches_complex_step(space, overlap, n_smooth, alphas):
+    """The particular problem on hat-Omega_i (particular="hat"): its reverse
+    pass (a source solve on the basis box, its face pressure in the pressure
+    rows) against the complex step of the forward variant on every parameter."""
+    prob = _problem((16, 16), seed=11 + space)
+    wp, wu = _seeds(prob, 3)
+    args = ((8, 8), overlap, space, alphas[0], alphas[1], n_smooth)
+    _, g = AD.mrcm_os_adjoint(prob, *args, wp, wu, particular="hat")
+    cs = np.array([_complex_step_variant(prob, j, args, wp, wu) for j in range(prob.ncells)])
+    scale = np.max(np.abs(cs))
+    assert np.max(np.abs(g - cs)) <= 1e-9 * scale, np.max(np.abs(g - cs)) / scale

@@ -118,8 +118,7 @@ typedef struct {
  *                pressures) like the basis functions.  No Omega_i operator is
  *                assembled or factored.  It shifts the affine local space and
  *                so changes the result (for overlap 0 the two coincide).
- *                2D and 3D; mrcm_adjoint and mrcm_backward return
- *                MRCM_ERR_UNSUPPORTED for it.
+ *                2D and 3D (the adjoint, like the method's, 2D).
  *                Other values: MRCM_ERR_BAD_INPUT. */
 typedef struct {
     int space;
@@ -255,8 +254,8 @@ int mrcm_set_permeability(mrcm_handle* h, const double* values, int is_log, int 
  * use); the interface system is solved transposed with its FP32 slab factors
  * and FP64 refinement.  Leaves the current solution unchanged.
  * MRCM_ERR_UNSUPPORTED for a member with no Dirichlet side (its pressure is
- * fixed only up to a constant), for 3D problems and for the particular
- * problem on hat-Omega_i.  Needs a solution (MRCM_ERR_STATE). */
+ * fixed only up to a constant) and for 3D problems.  Needs a solution
+ * (MRCM_ERR_STATE). */
 int mrcm_adjoint(mrcm_handle* h, const double* gp, const double* gu, double* g_logK, int device_ptrs);
 
 /* The same reverse pass with the seeds in (velocity, pressure) order and host

@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
         atomicExch(&P.status[2], job.item);
     }
 
-    const int nrhs = basis ? sd.nbasis : 1;
+    // with the particular problem on hat-Omega_i (a variant) it is the basis
+    // job's last right-hand side, k = nbasis, its vector in the per-box
+    // global scratch of the forward pass
+    const int nrhs = basis ? sd.nbasis + (Mth.part_hat ? 1 : 0) : 1;
     const int npsi = Mth.npsi;
     const int nxg = md.n[0];
     const double vol = md.h[0] * md.h[1];
@@ -442,7 +445,8 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
     for (int k = warp; k < nrhs; k += nw) {
         // forward solution x_k
         int sk = -1, mk = 0;
-        if (basis) {
+        const bool pk = !basis || k >= sd.nbasis;   // the particular problem
+        if (!pk) {
             int q = k / npsi;
             mk = k % npsi;
             for (int sid = 0; sid < 4; ++sid)
@@ -453,16 +457,17 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
             RhsBasis rb{sk, mk};
             warp_solve<T>(B, O, Sinv, cys, x, mixed ? wv : (T*)x, zb, rb, Mth.ir_tol, Mth.max_ir, &flags[1]);
         } else {
+            double* bs = basis ? P.bsrc + (size_t)job.item * P.dsc_stride : bsrc;
             for (int c = lane; c < B.n; c += 32)
-                bsrc[c] = source_rhs(B, O, fm, nxg, vol, ax, ay, nullptr, c % B.nx, c / B.nx);
+                bs[c] = source_rhs(B, O, fm, nxg, vol, ax, ay, nullptr, c % B.nx, c / B.nx);
             __syncwarp();
-            RhsStored rs{bsrc};
+            RhsStored rs{bs};
             warp_solve<T>(B, O, Sinv, cys, x, mixed ? wv : (T*)x, zb, rs, Mth.ir_tol, Mth.max_ir, &flags[1]);
         }
         __syncwarp();
         // adjoint right-hand side
-        const double xk = basis ? A.X[sd.col0 + k] : 1.0;
-        const int slot = basis ? k : P.nbasis_max;
+        const double xk = !pk ? A.X[sd.col0 + k] : 1.0;
+        const int slot = !pk ? k : P.nbasis_max;
         const double* gm = A.gmom + (((size_t)job.item * (P.nbasis_max + 1) + slot) * MRCM_MAXSIDE) * npsi * 2;
         for (int c = lane; c < B.n; c += 32) rt[c] = 0.0;
         __syncwarp();
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(128, 1) k_adj_local2d(DevPtrs P, MethodDev Mth
                 const int c = j * B.nx + i;
                 double ref = 0.0;
                 if (B.kind[sid] == 2) ref = (basis && sid == sk) ? psi_val(mk, pos, len, B.rlen[sid]) : 0.0;
-                else ref = basis ? 0.0 : B.val[sid];
+                else ref = pk ? B.val[sid] : 0.0;
                 atomicAdd(&gbT[side_off(B, sid) + pos], -mu[c] * (x[c] - ref));
             }
         }

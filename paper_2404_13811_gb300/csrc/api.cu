@@ -946,7 +946,8 @@ static int prepare_adjoint(mrcm_handle* h) {
     std::map<std::pair<int, int>, size_t> smem;
     for (int s = 0; s < nitems; ++s) {
         const SubDev& sd = h->sub[s];
-        for (int type = 0; type < 2; ++type) {
+        // (with the particular problem on hat-Omega_i the basis job carries it)
+        for (int type = 0; type < (h->mth.part_hat ? 1 : 2); ++type) {
             const int nx = type == JOB_BASIS ? sd.hih[0] - sd.loh[0] : sd.hi[0] - sd.lo[0];
             const int ny = type == JOB_BASIS ? sd.hih[1] - sd.loh[1] : sd.hi[1] - sd.lo[1];
             const int bw = nx <= 8 ? 8 : nx <= 16 ? 16 : nx <= 24 ? 24 : 32;
@@ -1710,8 +1711,6 @@ static int adjoint_body(mrcm_handle* h, const double* gp, const double* gu, doub
     if (!g_logK) return fail(h, MRCM_ERR_BAD_INPUT, "null output");
     if (h->stage != ST_SOLVED) return fail(h, MRCM_ERR_STATE, "mrcm_adjoint needs a solution");
     if (h->dim != 2) return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint is available for 2D problems");
-    if (h->mth.part_hat)
-        return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint is available for the particular problem on Omega_i");
     for (auto& md : h->mem)
         if (md.pure_neumann)
             return fail(h, MRCM_ERR_UNSUPPORTED, "the adjoint needs Dirichlet data on some side of every member");

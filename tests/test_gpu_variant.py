@@ -151,12 +151,25 @@ def test_hat_particular_3d(case, precision):
     _compare(prob, p, u, ref.p, ref.u, TOL[precision], f"3D case {case} {precision}")
 
 
-def test_hat_particular_has_no_adjoint():
-    from paper_2404_13811_gb300 import _lib as L
-    case = _case((32, 32), (16, 16), 2, 1, seed=7)
-    s = _solver(case, "fp64")
-    s.run(1)
-    with pytest.raises(L.MrcmError) as e:
-        s.adjoint(gp=np.ones(case.problem.ncells))
-    assert e.value.code == -7
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [0, 1])
+def test_hat_particular_gradient_matches_oracle_gradient(case, precision):
+    """mrcm_adjoint with the particular problem on hat-Omega_i against the
+    oracle's adjoint of the variant (itself pinned by complex step): max
+    |g - g_oracle| <= 1e-8 max |g_oracle|, as for the method."""
+    from oracle import mrcm_adjoint as AD
+    from paper_2404_13811_gb300.solver import MRCM
+    n, sub, ov, space, ab, as_, ns = [((64, 48), (16, 16), 2, 1, 1.0, 1.0, 2),
+                                      ((64, 32), (16, 16), 3, 0, 2.0, 0.5, 1)][case]
+    prob = I.lognormal_problem(n, sigma2=3.0, corr_len=0.15, seed=260 + case)
+    prob.f = np.random.default_rng(261 + case).standard_normal(prob.f.shape)
+    rng = np.random.default_rng(270 + case)
+    wp, wu = rng.standard_normal(prob.ncells), rng.standard_normal((prob.ncells, 4))
+    _, g_ref = AD.mrcm_os_adjoint(prob, sub, ov, space, ab, as_, ns, wp, wu, particular="hat")
+    s = MRCM(prob, I.Partition(sub, ov), space=space, alpha_basis=ab, alpha_smooth=as_, precision=precision,
+             particular="hat")
+    s.run(ns)
+    g = s.adjoint(wp, wu)
     s.close()
+    err = np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))
+    assert err <= 1e-8, err

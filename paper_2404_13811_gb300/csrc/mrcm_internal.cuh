@@ -86,7 +86,8 @@ struct DevPtrs {
     long long xs_stride;
     double* dsc;         // Jacobi scaling of the smoothing operator (mixed form)
     long long dsc_stride;
-    double* bsrc;        // 2D, particular problem on hat-Omega_i: its right-hand side [item][dsc_stride]
+    double* bsrc;        // particular problem on hat-Omega_i: scratch for its right-hand side [item][dsc_stride],
+                         // written and read within one kernel (null otherwise)
     // basis data
     double* Psi;         // [item][nbasis_max][ncell_i_max]
     double* Ug;          // [item][nbasis_max][2d][side_max]

@@ -138,7 +138,11 @@ typedef struct mrcm_handle mrcm_handle;
  *   device_ptrs  0: K and f are host pointers; 1: device pointers.
  *   cuda_stream  cudaStream_t on which all work of this handle runs (0 = legacy default).
  * Copies K and f, plans the decomposition, colours and interface ordering,
- * and allocates all device memory of the handle.  Synchronises the stream. */
+ * and allocates all device memory of the handle.  Synchronises the stream.
+ * On failure *out (when out is not NULL) still receives a handle that holds
+ * only the error text for mrcm_last_error; release it with mrcm_destroy.
+ * Argument checks (grid, partition, boundary kinds, params, host K and f)
+ * run on the host before any device work. */
 int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const mrcm_bc* bc,
                 const mrcm_partition* part, const mrcm_params* params, int device_ptrs,
                 void* cuda_stream, mrcm_handle** out);
@@ -147,7 +151,7 @@ int mrcm_create(const mrcm_grid* grid, const double* K, const double* f, const m
  * grids, bcs, parts have `count` entries; K[m], f[m] point at member m's
  * cells.  All members share `params`.  Every later call processes all
  * members together: one launch per kernel over all subdomains of all
- * members. */
+ * members.  Failure behaviour as mrcm_create. */
 int mrcm_create_batch(int count, const mrcm_grid* grids, const double* const* K,
                       const double* const* f, const mrcm_bc* bcs, const mrcm_partition* parts,
                       const mrcm_params* params, int device_ptrs, void* cuda_stream,

@@ -72,3 +72,13 @@ def test_variant_conserves_mass_every_stage():
 def test_variant_rejects_unknown_name():
     with pytest.raises(ValueError):
         O.mrcm_os(_het((16, 16), 1), (8, 8), 0, particular="gamma")
+
+
+def test_variant_conserves_mass_3d():
+    n = (12, 8, 8)
+    prob = I.lognormal_problem(n, sigma2=1.0, corr_len=0.3, seed=41, bc="left_right")
+    prob.f = np.random.default_rng(48).standard_normal(prob.f.shape)
+    r = O.mrcm_os(prob, (6, 4, 4), 1, space=1, n_smooth=1, keep_stages=True, particular="hat")
+    for key, (p, u) in r.stages.items():
+        scale = max(np.max(np.abs(prob.f)) * np.prod(prob.h), np.max(np.abs(u)) * prob.h[0] * prob.h[1])
+        assert np.max(np.abs(O.mass_residual(prob, u))) < 1e-12 * scale, key
